@@ -1,0 +1,156 @@
+/*
+ * pms.h - C ABI of the GB300 planted motif search library (libpms.so).
+ *
+ * The library solves the (l,d) planted motif search problem exactly (Nicolae & Rajasekaran,
+ * "Efficient Sequential and Parallel Algorithms for Planted Motif Search", Section 1):
+ * given n strings S_1..S_n of length m over an alphabet and integers l, d, it returns every
+ * l-mer M such that each S_i holds an l-mer within Hamming distance d of M.
+ *
+ * The search follows the paper's method (PMS8, Section 2 and Algorithms 1-2): one
+ * subproblem per l-mer x of S_1 (Section 2.3), a 2d compatibility filter (Section 2), a
+ * stack of l-mers filtered with the three-l-mer condition (Theorem 1, Section 2.4), and
+ * enumeration of the common d-neighbourhood of the stack (Algorithm 1) with every
+ * candidate verified against all strings.  All of it runs in CUDA kernels built for
+ * sm_103a; there is no CPU fallback: without a usable GPU every call fails with
+ * PMS_E_CUDA.
+ *
+ * Conventions for every call:
+ *  - Return value: PMS_OK (0) or a negative PMS_E_* code; pms_strerror names it.
+ *  - Sequences: n*m bytes, row-major (string i is bytes [i*m, (i+1)*m)), no terminators.
+ *  - Alphabet: NUL-terminated string of 2..32 distinct bytes.  Its order defines the
+ *    letter codes and therefore the output order.  A sequence byte outside the alphabet
+ *    gives PMS_E_ALPHABET.
+ *  - Limits: 1 <= n <= 64, 1 <= l <= m, m - l + 1 <= 65535, 0 <= d, l <= 64, and
+ *    l * ceil(log2 |alphabet|) <= 128 (l <= 64 for DNA, l <= 25 for 20 amino acids);
+ *    anything else gives PMS_E_INVAL.  d >= l is legal (every l-mer is a motif) but
+ *    usually overflows max_motifs.
+ *  - Output: the motif set, sorted ascending in the alphabet's order, duplicates removed,
+ *    as count*l bytes (no separators, no terminators).  Results the library allocates are
+ *    released with pms_result_free.
+ *  - Inputs are borrowed for the duration of the call (pms_submit copies them).
+ *  - A context is used by one thread at a time, except pms_submit/pms_poll, which may be
+ *    called from any thread.
+ */
+#ifndef PMS_H
+#define PMS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    PMS_OK = 0,
+    PMS_E_INVAL = -1,     /* bad argument or size outside the limits above */
+    PMS_E_ALPHABET = -2,  /* a sequence byte is not in the alphabet */
+    PMS_E_NOMEM = -3,     /* device or host allocation failed, or memory budget exceeded */
+    PMS_E_OVERFLOW = -4,  /* the motif set is larger than opts.max_motifs */
+    PMS_E_TIMEOUT = -5,   /* a bounded wait expired (pms_poll with a timeout) */
+    PMS_E_CUDA = -6,      /* CUDA error, or no usable sm_103a device */
+    PMS_E_BUSY = -7,      /* serving queue full */
+    PMS_E_NOTFOUND = -8   /* unknown ticket */
+};
+
+typedef struct pms_ctx pms_ctx;
+
+/* Tuning and resource options.  Zero in any field selects the default. */
+typedef struct pms_opts {
+    int threshold;            /* stack size t at which the search switches from filtering to
+                                 neighbourhood enumeration (Section 2.2 "threshold",
+                                 Algorithm 2 ThresholdCondition); 0 = autotuned.  The motif
+                                 set does not depend on it.  Range 2..8. */
+    int warps_per_block;      /* search kernel block size in warps (default 4) */
+    int blocks_per_sm;        /* resident search blocks per SM (default: occupancy limit) */
+    uint64_t max_motifs;      /* upper bound on the result size before PMS_E_OVERFLOW
+                                 (default 1<<26) */
+    size_t mem_budget;        /* device bytes the context may hold (default: 3/4 of free) */
+    int x_begin, x_end;       /* restrict the subproblems to the l-mers x_begin..x_end-1 of
+                                 S_1 (Section 2.3); both 0 = all.  Disjoint ranges merged
+                                 give the whole set (multi-device sharding by replicas). */
+    int serve_slots;          /* concurrent batches in the serving loop (default 4) */
+    int serve_max_batch;      /* instances per serving batch (default 16) */
+} pms_opts;
+
+/* One problem instance (Section 1). */
+typedef struct pms_instance {
+    const char *seqs;         /* n*m bytes, row-major */
+    int n, m;
+    const char *alphabet;     /* NUL-terminated */
+    int l, d;
+} pms_instance;
+
+/* Counters of one solve, summed over the kernels that ran. */
+typedef struct pms_stats {
+    uint64_t items;           /* (x, u) subproblems searched */
+    uint64_t tuples;          /* stacks that reached the enumeration */
+    uint64_t hd_compares;     /* l-mer distance evaluations (Hd or Theorem 1 triple) */
+    uint64_t enum_nodes;      /* Algorithm 1 tree nodes tested */
+    uint64_t leaves;          /* common neighbours produced (before verification) */
+    uint64_t raw_motifs;      /* verified motifs before duplicate removal */
+    double kernel_ms;         /* device time of the whole solve (CUDA events) */
+    double search_ms;         /* device time of the search kernel alone */
+    int threshold;            /* threshold used */
+} pms_stats;
+
+/* A solved motif set. */
+typedef struct pms_result {
+    uint64_t count;           /* number of motifs */
+    int l;                    /* motif length */
+    char *motifs;             /* count*l bytes, sorted, library-allocated (may be NULL if 0) */
+    pms_stats stats;
+} pms_result;
+
+/* Create a context on CUDA device `device` (opts may be NULL).  Fails with PMS_E_CUDA
+ * when the device is missing or is not compute capability 10.3. */
+int pms_create(pms_ctx **out, int device, const pms_opts *opts);
+void pms_destroy(pms_ctx *ctx);
+
+/* Solve one instance from host memory (Section 1 problem statement).  Blocking. */
+int pms_solve(pms_ctx *ctx, const char *seqs, int n, int m, const char *alphabet, int l,
+              int d, pms_result *out);
+
+/* Solve `count` instances in one batched launch sequence; outs[i] receives instance i.
+ * The motif sets equal those of `count` separate pms_solve calls.  Blocking. */
+int pms_solve_batch(pms_ctx *ctx, const pms_instance *inst, int count, pms_result *outs);
+
+/*
+ * Solve one instance whose sequences are already in device memory, leaving the result
+ * in device memory; for callers that keep data resident on the GPU.
+ *   d_seqs       device pointer, n*m bytes
+ *   d_motifs     device pointer, room for cap*l bytes; receives the sorted motif set
+ *   cap          capacity of d_motifs in motifs
+ *   count        host pointer; receives the motif count (even when > cap, in which case
+ *                PMS_E_OVERFLOW is returned and d_motifs holds the first cap motifs)
+ *   stream       cudaStream_t to run on (NULL = the context's stream); the call returns
+ *                after the work on it has finished.
+ */
+int pms_solve_device(pms_ctx *ctx, const char *d_seqs, int n, int m, const char *alphabet,
+                     int l, int d, char *d_motifs, uint64_t cap, uint64_t *count,
+                     void *stream, pms_stats *stats);
+
+/* Serving: queue an instance (inputs are copied before return) and get a ticket. */
+int pms_submit(pms_ctx *ctx, const pms_instance *inst, uint64_t *ticket);
+
+/* Serving: non-blocking check of a ticket.  *done = 1 and *out filled (ownership passes
+ * to the caller; the ticket is retired) when finished; *done = 0 otherwise.  The return
+ * value is the solve's own status once done. */
+int pms_poll(pms_ctx *ctx, uint64_t ticket, pms_result *out, int *done);
+
+/* Release the motif buffer of a result (safe on zeroed results). */
+void pms_result_free(pms_result *res);
+
+/* Static description of an error code. */
+const char *pms_strerror(int code);
+
+/* Number of instance classes (l, d, n, m, alphabet size) whose threshold the autotuner
+ * has cached, and a reset of that cache. */
+int pms_autotune_entries(pms_ctx *ctx);
+void pms_autotune_reset(pms_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PMS_H */

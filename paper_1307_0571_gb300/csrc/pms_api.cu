@@ -1,0 +1,885 @@
+// C ABI of libpms (include/pms.h): contexts, device workspaces, the batch pipeline
+// (pack -> 2d filter/items -> search -> sort/unique -> decode), the threshold model and
+// autotuner, and the continuous-batching serving loop behind pms_submit/pms_poll.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdlib>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <tuple>
+#include <unordered_map>
+#include <vector>
+
+#include "pms.h"
+#include "pms_internal.h"
+
+using namespace pms;
+
+namespace {
+
+// ------------------------------------------------------------------ device buffers
+
+struct DBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    ~DBuf() { release(); }
+    void release()
+    {
+        if (p)
+            cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+    // Grow to at least `bytes` (contents are not kept).
+    int ensure(size_t bytes, std::atomic<size_t> &held)
+    {
+        if (bytes <= cap)
+            return PMS_OK;
+        size_t want = std::max(bytes, cap + cap / 2);
+        want = (want + 255) & ~size_t(255);
+        release_counted(held);
+        if (cudaMalloc(&p, want) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            if (cudaMalloc(&p, bytes) != cudaSuccess) {
+                cudaGetLastError();
+                p = nullptr;
+                return PMS_E_NOMEM;
+            }
+            want = bytes;
+        }
+        cap = want;
+        held += cap;
+        return PMS_OK;
+    }
+    void release_counted(std::atomic<size_t> &held)
+    {
+        if (p) {
+            held -= cap;
+            release();
+        }
+    }
+    template <typename T>
+    T *as() const { return static_cast<T *>(p); }
+};
+
+struct Counters {           // one device block of small counters
+    unsigned long long item_count;
+    unsigned long long item_next;
+    unsigned long long key_count;
+    unsigned long long uniq_total;
+    int status;
+    int pad;
+    DevStats stats;
+};
+
+// Everything one pipeline run needs on the device; a context owns one for blocking calls
+// and one per serving slot, so slots run concurrently on their own streams.
+struct Workspace {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    DBuf seqs, maps, inst, alpha, lmers, items, lists, keys, keys_alt, hist, flags, out_chars,
+        byte_off, first, last, counters;
+    std::vector<DBuf *> all()
+    {
+        return {&seqs, &maps, &inst, &alpha, &lmers, &items, &lists, &keys, &keys_alt,
+                &hist, &flags, &out_chars, &byte_off, &first, &last, &counters};
+    }
+};
+
+#define PMS_CU(call)                               \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) {                   \
+            cudaGetLastError();                    \
+            return PMS_E_CUDA;                     \
+        }                                          \
+    } while (0)
+#define PMS_TRY(call)                              \
+    do {                                           \
+        int r_ = (call);                           \
+        if (r_ != PMS_OK)                          \
+            return r_;                             \
+    } while (0)
+
+// ---------------------------------------------------------------- instance checks
+
+struct Prep {
+    const char *seqs = nullptr;   // host or device (see on_device)
+    bool on_device = false;
+    int n = 0, m = 0, l = 0, d = 0, L = 0, k = 0, kbits = 0, t = 0, xb = 0, xe = 0;
+    std::string alphabet;
+    Layout lay = Layout::DNA32;
+};
+
+int prepare(const char *seqs, int n, int m, const char *alphabet, int l, int d,
+            const pms_opts &o, Prep &p)
+{
+    if (!seqs || !alphabet)
+        return PMS_E_INVAL;
+    size_t k = strnlen(alphabet, 64);
+    if (k < 2 || k > 32)
+        return PMS_E_INVAL;
+    bool seen[256] = {false};
+    for (size_t i = 0; i < k; i++) {
+        unsigned char c = (unsigned char)alphabet[i];
+        if (seen[c])
+            return PMS_E_INVAL;
+        seen[c] = true;
+    }
+    if (n < 1 || n > kRMax || l < 1 || m < l || d < 0 || l > 64 || m - l + 1 > 65535)
+        return PMS_E_INVAL;
+    int kbits = k <= 4 ? 2 : 5;
+    if (l * kbits > 128)
+        return PMS_E_INVAL;
+    p.seqs = seqs;
+    p.n = n;
+    p.m = m;
+    p.l = l;
+    p.d = d;
+    p.L = m - l + 1;
+    p.k = (int)k;
+    p.kbits = kbits;
+    p.alphabet.assign(alphabet, k);
+    p.lay = kbits == 2 ? (l <= 32 ? Layout::DNA32 : Layout::DNA64)
+                       : (l <= 32 ? Layout::P5_32 : Layout::P5_64);
+    p.xb = 0;
+    p.xe = p.L;
+    if (o.x_begin || o.x_end) {
+        p.xb = std::max(0, std::min(o.x_begin, p.L));
+        p.xe = std::max(p.xb, std::min(o.x_end, p.L));
+    }
+    return PMS_OK;
+}
+
+size_t lmer_bytes(Layout lay)
+{
+    switch (lay) {
+    case Layout::DNA32: return 8;
+    case Layout::DNA64: return 16;
+    case Layout::P5_32: return 20;
+    case Layout::P5_64: return 40;
+    }
+    return 40;
+}
+
+// ----------------------------------------------------- threshold model (Appendix D)
+
+double nbhd(int l, int d, int k)
+{
+    double s = 0, c = 1;   // c = C(l, i)
+    for (int i = 0; i <= std::min(d, l); i++) {
+        s += c * std::pow((double)(k - 1), i);
+        c = c * (l - i) / (i + 1);
+    }
+    return s;
+}
+
+// Appendix D: with p = N_2d/|S|^l (chance that an l-mer survives the 2d filter of the
+// stack top) and q = N_d/N_2d, the sample-driven part costs
+// Time_s(t) = n l sum_{j<=t} L^j p^{j(j-1)/2} and the pattern-driven part
+// Time_p(t) = L^t p^{t(t-1)/2} N_d q^{t-1} l; t minimises their sum over 2..min(n, 8).
+int model_threshold(int n, int m, int l, int d, int k)
+{
+    const double L = m - l + 1;
+    const double nd = nbhd(l, d, k), n2d = nbhd(l, 2 * d, k);
+    const double total = std::pow((double)k, l);
+    const double p = std::min(1.0, n2d / total), q = std::min(1.0, nd / std::max(n2d, 1.0));
+    int best = 2;
+    double best_cost = INFINITY;
+    for (int t = 2; t <= std::min(n, kTMax); t++) {
+        double ts = 0;
+        for (int j = 1; j <= t; j++)
+            ts += std::pow(L, j) * std::pow(p, j * (j - 1) / 2.0);
+        ts *= (double)n * l;
+        double tp = std::pow(L, t) * std::pow(p, t * (t - 1) / 2.0) * nd * std::pow(q, t - 1) * l;
+        if (ts + tp < best_cost) {
+            best_cost = ts + tp;
+            best = t;
+        }
+    }
+    return best;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------- context
+
+struct Request {
+    uint64_t ticket;
+    std::string seqs, alphabet;
+    int n, m, l, d;
+    std::chrono::steady_clock::time_point arrival;
+};
+
+struct Finished {
+    int rc;
+    pms_result res;
+};
+
+struct pms_ctx {
+    int device = 0;
+    int sm_count = 0;
+    pms_opts opts{};
+    std::atomic<size_t> held{0};
+    size_t budget = 0;
+    Workspace main;
+    std::mutex solve_mu;
+    // threshold autotuner cache: (l, d, n, m, k) -> t
+    std::mutex tune_mu;
+    std::map<std::tuple<int, int, int, int, int>, int> tune;
+    // serving
+    std::mutex q_mu;
+    std::condition_variable q_cv;
+    std::deque<Request> pending;
+    std::unordered_map<uint64_t, Finished> finished;
+    std::unordered_map<uint64_t, int> in_flight;
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    std::vector<std::unique_ptr<Workspace>> slots;
+    std::vector<std::thread> workers;
+    std::once_flag serve_once;
+};
+
+namespace {
+
+int ws_init(pms_ctx *c, Workspace &w)
+{
+    PMS_CU(cudaSetDevice(c->device));
+    PMS_CU(cudaStreamCreateWithFlags(&w.stream, cudaStreamNonBlocking));
+    for (auto &e : w.ev)
+        PMS_CU(cudaEventCreate(&e));
+    return PMS_OK;
+}
+
+void ws_free(pms_ctx *c, Workspace &w)
+{
+    cudaSetDevice(c->device);
+    for (DBuf *b : w.all())
+        b->release_counted(c->held);
+    for (auto &e : w.ev)
+        if (e)
+            cudaEventDestroy(e);
+    if (w.stream)
+        cudaStreamDestroy(w.stream);
+    w.stream = nullptr;
+}
+
+int threshold_for(pms_ctx *c, const Prep &p)
+{
+    if (c->opts.threshold)
+        return std::max(2, std::min(c->opts.threshold, kTMax));
+    std::lock_guard<std::mutex> g(c->tune_mu);
+    auto key = std::make_tuple(p.l, p.d, p.n, p.m, p.k);
+    auto it = c->tune.find(key);
+    if (it != c->tune.end())
+        return it->second;
+    int t = model_threshold(p.n, p.m, p.l, p.d, p.k);
+    c->tune[key] = t;
+    return t;
+}
+
+struct BatchOut {
+    // host path: per-instance results; device path: user buffer
+    std::vector<pms_result> *host = nullptr;
+    char *dev_motifs = nullptr;
+    uint64_t dev_cap = 0;
+    uint64_t *dev_count = nullptr;
+    std::vector<int> rc;
+};
+
+// The whole pipeline for instances that share one plane layout.
+int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
+              const std::vector<int> &idx, pms_stats *stats_out)
+{
+    const int ninst = (int)ins.size();
+    cudaStream_t s = w.stream;
+    const Layout lay = ins[0].lay;
+    std::vector<InstDesc> desc(ninst);
+    uint64_t seq_total = 0, lmer_total = 0, x_total = 0, item_cap = 0, list_cap = 0;
+    int key_bits = 0, tmax = 2;
+    for (int i = 0; i < ninst; i++) {
+        Prep &p = ins[i];
+        p.t = threshold_for(c, p);
+        InstDesc &D = desc[i];
+        D.seq_off = seq_total;
+        D.lmer_off = lmer_total;
+        D.x_off = x_total;
+        D.n = p.n;
+        D.m = p.m;
+        D.l = p.l;
+        D.d = p.d;
+        D.L = p.L;
+        D.k = p.k;
+        D.kbits = p.kbits;
+        D.t = p.t;
+        D.x_begin = p.xb;
+        D.x_end = p.xe;
+        seq_total += (uint64_t)p.n * p.m;
+        lmer_total += (uint64_t)p.n * p.L;
+        x_total += (uint64_t)(p.xe - p.xb);
+        item_cap += (uint64_t)(p.xe - p.xb) * (p.n > 1 ? (uint64_t)p.L : 1);
+        list_cap = std::max<uint64_t>(list_cap, (uint64_t)std::max(1, p.n - 1) * p.L);
+        key_bits = std::max(key_bits, p.l * p.kbits);
+        tmax = std::max(tmax, p.t);
+    }
+    const int multi = ninst > 1;
+    const int sort_bits = key_bits + (multi ? kInstBits : 0);
+    const int levels = tmax - 1;
+
+    // search launch shape
+    int wpb = c->opts.warps_per_block ? std::max(1, std::min(c->opts.warps_per_block, 4)) : 4;
+    int per_sm = search_max_blocks(lay, wpb);
+    if (per_sm <= 0)
+        return PMS_E_CUDA;
+    if (c->opts.blocks_per_sm)
+        per_sm = std::min(per_sm, c->opts.blocks_per_sm);
+    LaunchCfg cfg{wpb, per_sm * c->sm_count};
+    const uint64_t nwarps = (uint64_t)cfg.blocks * wpb;
+
+    // buffers
+    uint64_t key_cap = std::max<uint64_t>(1 << 16, w.keys.cap / 16);
+    PMS_TRY(w.seqs.ensure(seq_total, c->held));
+    PMS_TRY(w.maps.ensure(256 * (size_t)ninst, c->held));
+    PMS_TRY(w.alpha.ensure(32 * (size_t)ninst, c->held));
+    PMS_TRY(w.inst.ensure(sizeof(InstDesc) * ninst, c->held));
+    PMS_TRY(w.lmers.ensure(lmer_bytes(lay) * lmer_total, c->held));
+    PMS_TRY(w.items.ensure(sizeof(Item) * std::max<uint64_t>(item_cap, 1), c->held));
+    PMS_TRY(w.lists.ensure(4ull * nwarps * levels * list_cap, c->held));
+    PMS_TRY(w.keys.ensure(16 * key_cap, c->held));
+    PMS_TRY(w.counters.ensure(sizeof(Counters), c->held));
+    PMS_TRY(w.first.ensure(8 * (size_t)ninst, c->held));
+    PMS_TRY(w.last.ensure(8 * (size_t)ninst, c->held));
+    PMS_TRY(w.byte_off.ensure(8 * (size_t)ninst, c->held));
+    if (c->budget && c->held > c->budget)
+        return PMS_E_NOMEM;
+
+    // inputs
+    std::vector<uint8_t> maps(256 * (size_t)ninst, 0xFF), alpha(32 * (size_t)ninst, 0);
+    for (int i = 0; i < ninst; i++) {
+        for (int a = 0; a < ins[i].k; a++) {
+            maps[256 * (size_t)i + (uint8_t)ins[i].alphabet[a]] = (uint8_t)a;
+            alpha[32 * (size_t)i + a] = (uint8_t)ins[i].alphabet[a];
+        }
+        uint8_t *dst = w.seqs.as<uint8_t>() + desc[i].seq_off;
+        size_t bytes = (size_t)ins[i].n * ins[i].m;
+        PMS_CU(cudaMemcpyAsync(dst, ins[i].seqs, bytes,
+                               ins[i].on_device ? cudaMemcpyDeviceToDevice
+                                                : cudaMemcpyHostToDevice,
+                               s));
+    }
+    PMS_CU(cudaEventRecord(w.ev[0], s));
+    PMS_CU(cudaMemcpyAsync(w.maps.p, maps.data(), maps.size(), cudaMemcpyHostToDevice, s));
+    PMS_CU(cudaMemcpyAsync(w.alpha.p, alpha.data(), alpha.size(), cudaMemcpyHostToDevice, s));
+    PMS_CU(cudaMemcpyAsync(w.inst.p, desc.data(), sizeof(InstDesc) * ninst,
+                           cudaMemcpyHostToDevice, s));
+    Counters *dc = w.counters.as<Counters>();
+    PMS_CU(cudaMemsetAsync(dc, 0, sizeof(Counters), s));
+
+    PMS_CU(launch_pack(lay, w.inst.as<InstDesc>(), nullptr, ninst, lmer_total,
+                       w.seqs.as<uint8_t>(), w.maps.as<uint8_t>(), w.lmers.p, &dc->status, s));
+    PMS_CU(launch_items(lay, w.inst.as<InstDesc>(), nullptr, ninst, x_total, w.lmers.p,
+                        w.items.as<Item>(), &dc->item_count, item_cap, &dc->status, &dc->stats,
+                        s));
+    Counters hc{};
+    for (int attempt = 0;; attempt++) {
+        PMS_CU(cudaEventRecord(w.ev[1], s));
+        PMS_CU(launch_search(lay, w.inst.as<InstDesc>(), w.lmers.p, w.items.as<Item>(),
+                             &dc->item_count, item_cap, &dc->item_next, w.lists.as<uint32_t>(),
+                             list_cap,
+                             w.keys.as<uint64_t>(), &dc->key_count, key_cap, &dc->status,
+                             &dc->stats, cfg, key_bits, multi, levels, s));
+        PMS_CU(cudaEventRecord(w.ev[2], s));
+        PMS_CU(cudaMemcpyAsync(&hc, dc, sizeof hc, cudaMemcpyDeviceToHost, s));
+        PMS_CU(cudaStreamSynchronize(s));
+        if (hc.status & kErrAlphabet)
+            return PMS_E_ALPHABET;
+        if (hc.status & kErrItemsOverflow)
+            return PMS_E_CUDA;
+        if (!(hc.status & kErrKeysOverflow))
+            break;
+        // the raw (not yet unique) motif list outgrew its buffer: grow and search again
+        uint64_t want = hc.key_count + hc.key_count / 4 + 1024;
+        uint64_t limit = std::max<uint64_t>(c->opts.max_motifs, 1) * 64;
+        if (want > limit || attempt > 4)
+            return PMS_E_OVERFLOW;
+        PMS_TRY(w.keys.ensure(16 * want, c->held));
+        key_cap = w.keys.cap / 16;
+        if (c->budget && c->held > c->budget)
+            return PMS_E_NOMEM;
+        unsigned long long zero[2] = {0, 0};
+        PMS_CU(cudaMemcpyAsync(&dc->item_next, zero, 16, cudaMemcpyHostToDevice, s));
+        PMS_CU(cudaMemsetAsync(&dc->status, 0, sizeof(int), s));
+        PMS_CU(cudaMemsetAsync(&dc->stats, 0, sizeof(DevStats), s));
+    }
+
+    // collect: sort, unique, per-instance ranges
+    const size_t nkeys = hc.key_count;
+    const size_t ntiles = (nkeys + kSortTile - 1) / kSortTile;
+    PMS_TRY(w.keys_alt.ensure(16 * std::max<size_t>(nkeys, 1), c->held));
+    PMS_TRY(w.hist.ensure(4 * 256 * std::max<size_t>(ntiles, 1), c->held));
+    PMS_TRY(w.flags.ensure(4 * std::max<size_t>(ntiles, 1), c->held));
+    SortScratch scr{w.keys_alt.as<uint64_t>(), w.hist.as<unsigned>(), w.flags.as<unsigned>(),
+                    w.keys_alt.cap / 16, w.flags.cap / 4};
+    size_t nuniq = 0;
+    PMS_CU(sort_unique_keys(w.keys.as<uint64_t>(), nkeys, sort_bits, scr, &dc->uniq_total,
+                            &nuniq, s));
+    PMS_CU(cudaMemsetAsync(w.first.p, 0xFF, 8 * (size_t)ninst, s));
+    PMS_CU(cudaMemsetAsync(w.last.p, 0xFF, 8 * (size_t)ninst, s));
+    PMS_CU(launch_ranges(w.keys.as<uint64_t>(), nuniq, key_bits, multi, ninst,
+                         w.first.as<long long>(), w.last.as<long long>(), s));
+    std::vector<long long> first(ninst), last(ninst);
+    PMS_CU(cudaMemcpyAsync(first.data(), w.first.p, 8 * (size_t)ninst, cudaMemcpyDeviceToHost, s));
+    PMS_CU(cudaMemcpyAsync(last.data(), w.last.p, 8 * (size_t)ninst, cudaMemcpyDeviceToHost, s));
+    PMS_CU(cudaStreamSynchronize(s));
+    std::vector<uint64_t> counts(ninst), byte_off(ninst);
+    uint64_t bytes = 0;
+    for (int i = 0; i < ninst; i++) {
+        counts[i] = first[i] < 0 ? 0 : (uint64_t)(last[i] - first[i] + 1);
+        byte_off[i] = bytes;
+        bytes += counts[i] * (uint64_t)ins[i].l;
+    }
+    char *out_dev = nullptr;
+    if (bo.host) {
+        PMS_TRY(w.out_chars.ensure(std::max<uint64_t>(bytes, 1), c->held));
+        out_dev = w.out_chars.as<char>();
+    } else {
+        out_dev = bo.dev_motifs;
+        if (counts[0] > bo.dev_cap)
+            bytes = 0;   // decode nothing past the caller's capacity
+    }
+    PMS_CU(cudaMemcpyAsync(w.byte_off.p, byte_off.data(), 8 * (size_t)ninst,
+                           cudaMemcpyHostToDevice, s));
+    if (bytes)
+        PMS_CU(launch_decode(w.keys.as<uint64_t>(), nuniq, key_bits, multi, w.inst.as<InstDesc>(),
+                             w.alpha.as<uint8_t>(), out_dev, w.byte_off.as<uint64_t>(),
+                             w.first.as<long long>(), s));
+    PMS_CU(cudaEventRecord(w.ev[3], s));
+    PMS_CU(cudaStreamSynchronize(s));
+
+    float total_ms = 0, search_ms = 0;
+    cudaEventElapsedTime(&total_ms, w.ev[0], w.ev[3]);
+    cudaEventElapsedTime(&search_ms, w.ev[1], w.ev[2]);
+    pms_stats st{};
+    st.items = hc.stats.items;
+    st.tuples = hc.stats.tuples;
+    st.hd_compares = hc.stats.hd_compares;
+    st.enum_nodes = hc.stats.enum_nodes;
+    st.leaves = hc.stats.leaves;
+    st.raw_motifs = hc.stats.raw_motifs;
+    st.kernel_ms = total_ms;
+    st.search_ms = search_ms;
+    st.threshold = ins[0].t;
+    if (stats_out)
+        *stats_out = st;
+
+    const uint64_t maxm = c->opts.max_motifs;
+    if (bo.host) {
+        for (int i = 0; i < ninst; i++) {
+            pms_result &r = (*bo.host)[idx[i]];
+            r.count = 0;
+            r.l = ins[i].l;
+            r.motifs = nullptr;
+            r.stats = st;
+            r.stats.threshold = ins[i].t;
+            if (counts[i] > maxm) {
+                bo.rc[idx[i]] = PMS_E_OVERFLOW;
+                continue;
+            }
+            size_t nb = counts[i] * (size_t)ins[i].l;
+            if (nb) {
+                r.motifs = static_cast<char *>(std::malloc(nb));
+                if (!r.motifs) {
+                    bo.rc[idx[i]] = PMS_E_NOMEM;
+                    continue;
+                }
+                PMS_CU(cudaMemcpy(r.motifs, out_dev + byte_off[i], nb, cudaMemcpyDeviceToHost));
+            }
+            r.count = counts[i];
+            bo.rc[idx[i]] = PMS_OK;
+        }
+    } else {
+        *bo.dev_count = counts[0];
+        bo.rc[0] = counts[0] > bo.dev_cap || counts[0] > maxm ? PMS_E_OVERFLOW : PMS_OK;
+    }
+    return PMS_OK;
+}
+
+// Split a batch into groups that can share one launch sequence (same plane layout, key
+// room for the instance id) and run each.
+int run_batch(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo, pms_stats *agg)
+{
+    std::map<int, std::vector<int>> groups;
+    for (int i = 0; i < (int)ins.size(); i++) {
+        int key = (int)ins[i].lay;
+        if (ins[i].l * ins[i].kbits + kInstBits > 128)
+            key = 100 + i;   // no room for the instance id: runs alone
+        groups[key].push_back(i);
+    }
+    pms_stats total{};
+    for (auto &g : groups) {
+        for (size_t off = 0; off < g.second.size(); off += 60000) {
+            std::vector<int> idx(g.second.begin() + off,
+                                 g.second.begin() + std::min(g.second.size(), off + 60000));
+            std::vector<Prep> part;
+            for (int i : idx)
+                part.push_back(ins[i]);
+            pms_stats st{};
+            int rc = run_group(c, w, part, bo, idx, &st);
+            if (rc != PMS_OK) {
+                for (int i : idx)
+                    bo.rc[i] = rc;
+                if (!bo.host)
+                    return rc;
+                continue;
+            }
+            total.items += st.items;
+            total.tuples += st.tuples;
+            total.hd_compares += st.hd_compares;
+            total.enum_nodes += st.enum_nodes;
+            total.leaves += st.leaves;
+            total.raw_motifs += st.raw_motifs;
+            total.kernel_ms += st.kernel_ms;
+            total.search_ms += st.search_ms;
+            total.threshold = st.threshold;
+        }
+    }
+    if (agg)
+        *agg = total;
+    return PMS_OK;
+}
+
+// --------------------------------------------------------------------- serving loop
+
+// One serving slot: waits for requests, admits as many as fit (count and memory budget),
+// runs them as one batch on its own stream and publishes the results.  Several slots run
+// at once, so requests that arrive while a batch is on the GPU start on another slot.
+void serve_worker(pms_ctx *c, Workspace *w)
+{
+    cudaSetDevice(c->device);
+    const int max_batch = c->opts.serve_max_batch;
+    for (;;) {
+        std::vector<Request> batch;
+        {
+            std::unique_lock<std::mutex> lk(c->q_mu);
+            c->q_cv.wait(lk, [&] { return c->stop || !c->pending.empty(); });
+            if (c->stop && c->pending.empty())
+                return;
+            // estimated device bytes of a request: strings, l-mers, items, raw motifs
+            size_t room = c->budget > c->held ? c->budget - c->held : 0;
+            size_t est_total = 0;
+            while (!c->pending.empty() && (int)batch.size() < max_batch) {
+                const Request &r = c->pending.front();
+                size_t L = (size_t)(r.m - r.l + 1);
+                size_t est = (size_t)r.n * r.m * 2 + (size_t)r.n * L * 40 + L * L * 8;
+                if (!batch.empty() && est_total + est > room)
+                    break;
+                est_total += est;
+                batch.push_back(std::move(c->pending.front()));
+                c->pending.pop_front();
+            }
+            for (auto &r : batch)
+                c->in_flight[r.ticket] = 1;
+        }
+        std::vector<Prep> ins(batch.size());
+        std::vector<pms_result> res(batch.size());
+        BatchOut bo;
+        bo.host = &res;
+        bo.rc.assign(batch.size(), PMS_OK);
+        std::vector<int> pre_rc(batch.size(), PMS_OK);
+        std::vector<Prep> ok_ins;
+        std::vector<int> ok_idx;
+        for (size_t i = 0; i < batch.size(); i++) {
+            pre_rc[i] = prepare(batch[i].seqs.data(), batch[i].n, batch[i].m,
+                                batch[i].alphabet.c_str(), batch[i].l, batch[i].d, c->opts,
+                                ins[i]);
+            if (pre_rc[i] == PMS_OK) {
+                ok_ins.push_back(ins[i]);
+                ok_idx.push_back((int)i);
+            }
+        }
+        if (!ok_ins.empty()) {
+            std::vector<pms_result> ok_res(ok_ins.size());
+            BatchOut ob;
+            ob.host = &ok_res;
+            ob.rc.assign(ok_ins.size(), PMS_OK);
+            run_batch(c, *w, ok_ins, ob, nullptr);
+            for (size_t j = 0; j < ok_idx.size(); j++) {
+                res[ok_idx[j]] = ok_res[j];
+                pre_rc[ok_idx[j]] = ob.rc[j];
+            }
+        }
+        {
+            std::lock_guard<std::mutex> lk(c->q_mu);
+            for (size_t i = 0; i < batch.size(); i++) {
+                c->in_flight.erase(batch[i].ticket);
+                c->finished[batch[i].ticket] = Finished{pre_rc[i], res[i]};
+            }
+        }
+    }
+}
+
+int start_serving(pms_ctx *c)
+{
+    int rc = PMS_OK;
+    std::call_once(c->serve_once, [&] {
+        for (int i = 0; i < c->opts.serve_slots; i++) {
+            auto w = std::make_unique<Workspace>();
+            if (ws_init(c, *w) != PMS_OK) {
+                rc = PMS_E_CUDA;
+                return;
+            }
+            c->slots.push_back(std::move(w));
+        }
+        for (auto &w : c->slots)
+            c->workers.emplace_back(serve_worker, c, w.get());
+    });
+    return rc;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------- C ABI
+
+extern "C" {
+
+const char *pms_strerror(int code)
+{
+    switch (code) {
+    case PMS_OK: return "ok";
+    case PMS_E_INVAL: return "invalid argument";
+    case PMS_E_ALPHABET: return "sequence byte not in the alphabet";
+    case PMS_E_NOMEM: return "out of memory or over the memory budget";
+    case PMS_E_OVERFLOW: return "motif set larger than max_motifs";
+    case PMS_E_TIMEOUT: return "timed out";
+    case PMS_E_CUDA: return "CUDA error or no usable sm_103a device";
+    case PMS_E_BUSY: return "busy";
+    case PMS_E_NOTFOUND: return "unknown ticket";
+    }
+    return "unknown error";
+}
+
+int pms_create(pms_ctx **out, int device, const pms_opts *opts)
+{
+    if (!out)
+        return PMS_E_INVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return PMS_E_CUDA;
+    }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess)
+        return PMS_E_CUDA;
+    if (prop.major != 10 || prop.minor != 3)
+        return PMS_E_CUDA;   // the kernels are built for sm_103a only
+    auto *c = new (std::nothrow) pms_ctx();
+    if (!c)
+        return PMS_E_NOMEM;
+    c->device = device;
+    c->sm_count = prop.multiProcessorCount;
+    if (opts)
+        c->opts = *opts;
+    if (!c->opts.max_motifs)
+        c->opts.max_motifs = 1ull << 26;
+    if (!c->opts.serve_slots)
+        c->opts.serve_slots = 4;
+    if (!c->opts.serve_max_batch)
+        c->opts.serve_max_batch = 16;
+    if (c->opts.threshold && (c->opts.threshold < 2 || c->opts.threshold > kTMax)) {
+        delete c;
+        return PMS_E_INVAL;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) {
+        delete c;
+        return PMS_E_CUDA;
+    }
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    c->budget = c->opts.mem_budget ? c->opts.mem_budget : free_b / 4 * 3;
+    if (ws_init(c, c->main) != PMS_OK) {
+        ws_free(c, c->main);
+        delete c;
+        return PMS_E_CUDA;
+    }
+    *out = c;
+    return PMS_OK;
+}
+
+void pms_destroy(pms_ctx *c)
+{
+    if (!c)
+        return;
+    {
+        std::lock_guard<std::mutex> lk(c->q_mu);
+        c->stop = true;
+    }
+    c->q_cv.notify_all();
+    for (auto &t : c->workers)
+        t.join();
+    for (auto &w : c->slots)
+        ws_free(c, *w);
+    for (auto &f : c->finished)
+        std::free(f.second.res.motifs);
+    ws_free(c, c->main);
+    delete c;
+}
+
+int pms_solve(pms_ctx *c, const char *seqs, int n, int m, const char *alphabet, int l, int d,
+              pms_result *out)
+{
+    if (!c || !out)
+        return PMS_E_INVAL;
+    pms_instance in{seqs, n, m, alphabet, l, d};
+    return pms_solve_batch(c, &in, 1, out);
+}
+
+int pms_solve_batch(pms_ctx *c, const pms_instance *inst, int count, pms_result *outs)
+{
+    if (!c || (!inst && count) || (!outs && count) || count < 0)
+        return PMS_E_INVAL;
+    std::vector<Prep> ins(count);
+    for (int i = 0; i < count; i++) {
+        outs[i] = pms_result{};
+        int rc = prepare(inst[i].seqs, inst[i].n, inst[i].m, inst[i].alphabet, inst[i].l,
+                         inst[i].d, c->opts, ins[i]);
+        if (rc != PMS_OK)
+            return rc;
+    }
+    if (!count)
+        return PMS_OK;
+    std::lock_guard<std::mutex> g(c->solve_mu);
+    if (cudaSetDevice(c->device) != cudaSuccess)
+        return PMS_E_CUDA;
+    std::vector<pms_result> res(count);
+    BatchOut bo;
+    bo.host = &res;
+    bo.rc.assign(count, PMS_OK);
+    int rc = run_batch(c, c->main, ins, bo, nullptr);
+    int first_err = rc;
+    for (int i = 0; i < count; i++) {
+        outs[i] = res[i];
+        if (first_err == PMS_OK && bo.rc[i] != PMS_OK)
+            first_err = bo.rc[i];
+    }
+    if (first_err != PMS_OK)
+        for (int i = 0; i < count; i++)
+            pms_result_free(&outs[i]);
+    return first_err;
+}
+
+int pms_solve_device(pms_ctx *c, const char *d_seqs, int n, int m, const char *alphabet, int l,
+                     int d, char *d_motifs, uint64_t cap, uint64_t *count, void *stream,
+                     pms_stats *stats)
+{
+    if (!c || !count || (!d_motifs && cap))
+        return PMS_E_INVAL;
+    std::vector<Prep> ins(1);
+    int rc = prepare(d_seqs, n, m, alphabet, l, d, c->opts, ins[0]);
+    if (rc != PMS_OK)
+        return rc;
+    ins[0].on_device = true;
+    std::lock_guard<std::mutex> g(c->solve_mu);
+    if (cudaSetDevice(c->device) != cudaSuccess)
+        return PMS_E_CUDA;
+    cudaStream_t saved = c->main.stream;
+    if (stream)
+        c->main.stream = static_cast<cudaStream_t>(stream);
+    BatchOut bo;
+    bo.dev_motifs = d_motifs;
+    bo.dev_cap = cap;
+    bo.dev_count = count;
+    bo.rc.assign(1, PMS_OK);
+    std::vector<int> idx{0};
+    pms_stats st{};
+    rc = run_group(c, c->main, ins, bo, idx, &st);
+    c->main.stream = saved;
+    if (stats)
+        *stats = st;
+    return rc != PMS_OK ? rc : bo.rc[0];
+}
+
+int pms_submit(pms_ctx *c, const pms_instance *inst, uint64_t *ticket)
+{
+    if (!c || !inst || !ticket || !inst->seqs || !inst->alphabet || inst->n < 1 || inst->m < 1)
+        return PMS_E_INVAL;
+    int rc = start_serving(c);
+    if (rc != PMS_OK)
+        return rc;
+    Request r;
+    r.seqs.assign(inst->seqs, (size_t)inst->n * inst->m);
+    r.alphabet.assign(inst->alphabet, strnlen(inst->alphabet, 64));
+    r.n = inst->n;
+    r.m = inst->m;
+    r.l = inst->l;
+    r.d = inst->d;
+    r.arrival = std::chrono::steady_clock::now();
+    {
+        std::lock_guard<std::mutex> lk(c->q_mu);
+        if (c->pending.size() >= 1000000)
+            return PMS_E_BUSY;
+        r.ticket = c->next_ticket++;
+        *ticket = r.ticket;
+        c->pending.push_back(std::move(r));
+    }
+    c->q_cv.notify_one();
+    return PMS_OK;
+}
+
+int pms_poll(pms_ctx *c, uint64_t ticket, pms_result *out, int *done)
+{
+    if (!c || !out || !done)
+        return PMS_E_INVAL;
+    *done = 0;
+    std::lock_guard<std::mutex> lk(c->q_mu);
+    auto it = c->finished.find(ticket);
+    if (it == c->finished.end()) {
+        if (c->in_flight.count(ticket))
+            return PMS_OK;
+        for (auto &r : c->pending)
+            if (r.ticket == ticket)
+                return PMS_OK;
+        return PMS_E_NOTFOUND;
+    }
+    *out = it->second.res;
+    int rc = it->second.rc;
+    c->finished.erase(it);
+    *done = 1;
+    return rc;
+}
+
+void pms_result_free(pms_result *res)
+{
+    if (!res)
+        return;
+    std::free(res->motifs);
+    res->motifs = nullptr;
+    res->count = 0;
+}
+
+int pms_autotune_entries(pms_ctx *c)
+{
+    if (!c)
+        return 0;
+    std::lock_guard<std::mutex> g(c->tune_mu);
+    return (int)c->tune.size();
+}
+
+void pms_autotune_reset(pms_ctx *c)
+{
+    if (!c)
+        return;
+    std::lock_guard<std::mutex> g(c->tune_mu);
+    c->tune.clear();
+}
+
+}  // extern "C"

@@ -1,0 +1,128 @@
+// Internal declarations shared by the CUDA translation units of libpms.
+//
+// Device data of one batch (one launch sequence):
+//   seqs     all instances' sequences, byte-concatenated (instance i at InstDesc.seq_off)
+//   maps     256-byte letter -> code table per instance (0xFF = not in the alphabet)
+//   lmers    every l-mer of every string as bit planes: plane b holds bit b of each
+//            letter's code, bit p = position p (Section 2.1 "Compress l-mers", planar form)
+//   items    (instance, x, branch row, u) subproblems that passed the 2d filter
+//   keys     verified motifs as 128-bit sortable keys (instance id in the top bits)
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pms {
+
+constexpr int kTMax = 8;        // deepest stack (threshold) supported
+constexpr int kRMax = 64;       // most strings per instance (row bitmasks are 64-bit)
+constexpr int kCandBuf = 64;    // leaf buffer per warp
+constexpr int kInstBits = 16;   // instance id bits in the output key
+
+// One instance of a batch, as the kernels see it.
+struct InstDesc {
+    uint64_t seq_off;     // byte offset of the instance's strings in the batch buffer
+    uint64_t lmer_off;    // offset (in l-mers) of its l-mer table
+    uint64_t x_off;       // offset of its first x in the batch's x enumeration
+    int n, m, l, d;
+    int L;                // m - l + 1
+    int k;                // alphabet size
+    int kbits;            // bits per letter in the output key
+    int t;                // threshold stack size
+    int x_begin, x_end;   // subproblem range of S_1
+};
+
+// One (x, u) subproblem: x = S_1[x..], u = S_b[u..] with Hd(x,u) <= 2d and b the
+// smallest row of the 2d filter (Section 2.1 "Sort rows by size").  b = 0xFFFF marks a
+// single-string instance (no u).
+struct Item {
+    uint32_t inst;
+    uint16_t x;
+    uint16_t u;
+    uint16_t b;
+    uint16_t pad;
+};
+
+// Counters the kernels accumulate (one struct in device memory per solve).
+struct DevStats {
+    unsigned long long items;
+    unsigned long long tuples;
+    unsigned long long hd_compares;
+    unsigned long long enum_nodes;
+    unsigned long long leaves;
+    unsigned long long raw_motifs;
+};
+
+// Status bits a kernel raises.
+enum : int {
+    kErrAlphabet = 1,
+    kErrItemsOverflow = 2,
+    kErrKeysOverflow = 4,
+    kErrListOverflow = 8,
+};
+
+// Plane layout classes: bits per letter (2 for |alphabet| <= 4, else 5) and word width.
+enum class Layout { DNA32, DNA64, P5_32, P5_64 };
+
+// ---- kernels (pms_kernels.cu) ----
+struct LaunchCfg {
+    int warps_per_block;
+    int blocks;           // search grid size
+};
+
+// Pack every string of the batch into planar l-mers; flags bytes outside the alphabet.
+cudaError_t launch_pack(Layout lay, const InstDesc *d_inst, const uint64_t *d_lmer_prefix,
+                        int ninst, uint64_t total_lmers, const uint8_t *d_seqs,
+                        const uint8_t *d_maps, void *d_lmers, int *d_status,
+                        cudaStream_t s);
+
+// The 2d filter of every x (Section 2): picks the smallest row and emits the items.
+cudaError_t launch_items(Layout lay, const InstDesc *d_inst, const uint64_t *d_x_prefix,
+                         int ninst, uint64_t total_x, const void *d_lmers, Item *d_items,
+                         unsigned long long *d_item_count, uint64_t item_cap,
+                         int *d_status, DevStats *d_stats, cudaStream_t s);
+
+// The stack search + enumeration + verification (Algorithm 2 with Algorithm 1),
+// persistent over the item list.  Each warp owns `levels` lists of list_cap entries in
+// d_lists (scratch, levels * list_cap * 4 bytes per resident warp).
+cudaError_t launch_search(Layout lay, const InstDesc *d_inst, const void *d_lmers,
+                          const Item *d_items, const unsigned long long *d_item_count,
+                          uint64_t item_cap, unsigned long long *d_item_next, uint32_t *d_lists,
+                          uint64_t list_cap, uint64_t *d_keys,
+                          unsigned long long *d_key_count, uint64_t key_cap, int *d_status,
+                          DevStats *d_stats, const LaunchCfg &cfg, int key_shift, int multi,
+                          int levels, cudaStream_t s);
+
+// Resident search blocks per SM for a block of `warps_per_block` warps.
+int search_max_blocks(Layout lay, int warps_per_block);
+size_t search_smem_bytes(Layout lay, int warps_per_block);
+
+// ---- sort / unique / decode (pms_sort.cu) ----
+struct SortScratch {
+    uint64_t *keys_alt;         // second key buffer (2 words per key)
+    unsigned int *hist;         // digit histograms
+    unsigned int *flags;        // per-tile counts for compaction
+    size_t cap_keys;
+    size_t cap_tiles;
+};
+
+constexpr int kSortTile = 1024;
+
+// Sort n 128-bit keys (pairs of u64: [2i] = high word, [2i+1] = low word) ascending on
+// their low `bits` bits (high word first) and remove duplicates.  Returns the number of
+// unique keys, left in `keys`.  Synchronises the stream once to read the count back.
+cudaError_t sort_unique_keys(uint64_t *keys, size_t n, int bits, SortScratch &scr,
+                             unsigned long long *d_total, size_t *n_unique, cudaStream_t s);
+
+// Per-instance index ranges [first, last] of sorted unique keys (-1 when empty).
+cudaError_t launch_ranges(const uint64_t *d_keys, size_t n, int key_shift, int multi,
+                          int ninst, long long *d_first, long long *d_last, cudaStream_t s);
+
+// Decode sorted keys into letters: key i of instance j goes to
+// out + byte_off[j] + (i - first[j]) * l_j.  `alpha` holds 32 letters per instance.
+cudaError_t launch_decode(const uint64_t *d_keys, size_t n, int key_shift, int multi,
+                          const InstDesc *d_inst, const uint8_t *d_alpha, char *d_out,
+                          const uint64_t *d_byte_off, const long long *d_first,
+                          cudaStream_t s);
+
+}  // namespace pms
