@@ -89,6 +89,9 @@ typedef struct pms_stats {
     uint64_t enum_nodes;      /* Algorithm 1 tree nodes tested */
     uint64_t leaves;          /* common neighbours produced (before verification) */
     uint64_t raw_motifs;      /* verified motifs before duplicate removal */
+    uint64_t cyc_filter;      /* search-kernel SM cycles in filtering, summed over warps */
+    uint64_t cyc_enum;        /* ... in neighbourhood enumeration (Algorithm 1) */
+    uint64_t cyc_verify;      /* ... in verification (isMotif) */
     double kernel_ms;         /* device time of the whole solve (CUDA events) */
     double search_ms;         /* device time of the search kernel alone */
     int threshold;            /* threshold used */

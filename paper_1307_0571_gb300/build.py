@@ -17,7 +17,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libpms.so")
-SOURCES = ["pms_kernels.cu", "pms_sort.cu", "pms_api.cu"]
+SOURCES = ["pms_prep.cu", "pms_search_dna32.cu", "pms_search_dna64.cu", "pms_search_p5_32.cu",
+           "pms_search_p5_64.cu", "pms_sort.cu", "pms_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -86,11 +86,11 @@ struct Counters {           // one device block of small counters
 struct Workspace {
     cudaStream_t stream = nullptr;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-    DBuf seqs, maps, inst, alpha, lmers, items, lists, keys, keys_alt, hist, flags, out_chars,
-        byte_off, first, last, counters;
+    DBuf seqs, maps, inst, alpha, lmers, items, lists, fscr, keys, keys_alt, hist, flags,
+        out_chars, byte_off, first, last, counters;
     std::vector<DBuf *> all()
     {
-        return {&seqs, &maps, &inst, &alpha, &lmers, &items, &lists, &keys, &keys_alt,
+        return {&seqs, &maps, &inst, &alpha, &lmers, &items, &lists, &fscr, &keys, &keys_alt,
                 &hist, &flags, &out_chars, &byte_off, &first, &last, &counters};
     }
 };
@@ -273,7 +273,18 @@ void ws_free(pms_ctx *c, Workspace &w)
     w.stream = nullptr;
 }
 
+// Thresholds 2..4 enumerate with packed byte budgets, which hold d <= 41.
+int threshold_for_raw(pms_ctx *c, const Prep &p);
+
 int threshold_for(pms_ctx *c, const Prep &p)
+{
+    int t = threshold_for_raw(c, p);
+    if (p.d > 41 && t < 5)
+        t = std::min(5, kTMax);
+    return t;
+}
+
+int threshold_for_raw(pms_ctx *c, const Prep &p)
 {
     if (c->opts.threshold)
         return std::max(2, std::min(c->opts.threshold, kTMax));
@@ -305,10 +316,10 @@ int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
     const Layout lay = ins[0].lay;
     std::vector<InstDesc> desc(ninst);
     uint64_t seq_total = 0, lmer_total = 0, x_total = 0, item_cap = 0, list_cap = 0;
-    int key_bits = 0, tmax = 2;
+    int key_bits = 0, lmax = 1;
+    const int t = ins[0].t;   // every instance of a group shares the threshold
     for (int i = 0; i < ninst; i++) {
         Prep &p = ins[i];
-        p.t = threshold_for(c, p);
         InstDesc &D = desc[i];
         D.seq_off = seq_total;
         D.lmer_off = lmer_total;
@@ -329,15 +340,15 @@ int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
         item_cap += (uint64_t)(p.xe - p.xb) * (p.n > 1 ? (uint64_t)p.L : 1);
         list_cap = std::max<uint64_t>(list_cap, (uint64_t)std::max(1, p.n - 1) * p.L);
         key_bits = std::max(key_bits, p.l * p.kbits);
-        tmax = std::max(tmax, p.t);
+        lmax = std::max(lmax, p.l);
     }
     const int multi = ninst > 1;
     const int sort_bits = key_bits + (multi ? kInstBits : 0);
-    const int levels = tmax - 1;
+    const int levels = search_levels(t);
 
     // search launch shape
     int wpb = c->opts.warps_per_block ? std::max(1, std::min(c->opts.warps_per_block, 4)) : 4;
-    int per_sm = search_max_blocks(lay, wpb);
+    int per_sm = search_max_blocks(lay, t, wpb);
     if (per_sm <= 0)
         return PMS_E_CUDA;
     if (c->opts.blocks_per_sm)
@@ -354,6 +365,8 @@ int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
     PMS_TRY(w.lmers.ensure(lmer_bytes(lay) * lmer_total, c->held));
     PMS_TRY(w.items.ensure(sizeof(Item) * std::max<uint64_t>(item_cap, 1), c->held));
     PMS_TRY(w.lists.ensure(4ull * nwarps * levels * list_cap, c->held));
+    const uint64_t fstride = (search_frontier_bytes(lay, lmax) + 255) & ~uint64_t(255);
+    PMS_TRY(w.fscr.ensure(fstride * nwarps, c->held));
     PMS_TRY(w.keys.ensure(16 * key_cap, c->held));
     PMS_TRY(w.counters.ensure(sizeof(Counters), c->held));
     PMS_TRY(w.first.ensure(8 * (size_t)ninst, c->held));
@@ -392,11 +405,12 @@ int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
     Counters hc{};
     for (int attempt = 0;; attempt++) {
         PMS_CU(cudaEventRecord(w.ev[1], s));
-        PMS_CU(launch_search(lay, w.inst.as<InstDesc>(), w.lmers.p, w.items.as<Item>(),
-                             &dc->item_count, item_cap, &dc->item_next, w.lists.as<uint32_t>(),
-                             list_cap,
-                             w.keys.as<uint64_t>(), &dc->key_count, key_cap, &dc->status,
-                             &dc->stats, cfg, key_bits, multi, levels, s));
+        SearchArgs sa{w.inst.as<InstDesc>(), w.lmers.p, w.items.as<Item>(), &dc->item_count,
+                      item_cap, &dc->item_next, w.lists.as<uint32_t>(), list_cap,
+                      w.keys.as<uint64_t>(), &dc->key_count, key_cap, &dc->status,
+                      &dc->stats, key_bits, multi, cfg, w.fscr.as<unsigned char>(), fstride,
+                      lmax};
+        PMS_CU(launch_search(lay, t, sa, s));
         PMS_CU(cudaEventRecord(w.ev[2], s));
         PMS_CU(cudaMemcpyAsync(&hc, dc, sizeof hc, cudaMemcpyDeviceToHost, s));
         PMS_CU(cudaStreamSynchronize(s));
@@ -475,6 +489,9 @@ int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
     st.enum_nodes = hc.stats.enum_nodes;
     st.leaves = hc.stats.leaves;
     st.raw_motifs = hc.stats.raw_motifs;
+    st.cyc_filter = hc.stats.cyc_filter;
+    st.cyc_enum = hc.stats.cyc_enum;
+    st.cyc_verify = hc.stats.cyc_verify;
     st.kernel_ms = total_ms;
     st.search_ms = search_ms;
     st.threshold = ins[0].t;
@@ -519,9 +536,10 @@ int run_batch(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo, pm
 {
     std::map<int, std::vector<int>> groups;
     for (int i = 0; i < (int)ins.size(); i++) {
-        int key = (int)ins[i].lay;
+        ins[i].t = threshold_for(c, ins[i]);
+        int key = (int)ins[i].lay * 16 + ins[i].t;
         if (ins[i].l * ins[i].kbits + kInstBits > 128)
-            key = 100 + i;   // no room for the instance id: runs alone
+            key = 1000 + i;   // no room for the instance id: runs alone
         groups[key].push_back(i);
     }
     pms_stats total{};
@@ -547,6 +565,9 @@ int run_batch(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo, pm
             total.enum_nodes += st.enum_nodes;
             total.leaves += st.leaves;
             total.raw_motifs += st.raw_motifs;
+            total.cyc_filter += st.cyc_filter;
+            total.cyc_enum += st.cyc_enum;
+            total.cyc_verify += st.cyc_verify;
             total.kernel_ms += st.kernel_ms;
             total.search_ms += st.search_ms;
             total.threshold = st.threshold;
@@ -788,6 +809,7 @@ int pms_solve_device(pms_ctx *c, const char *d_seqs, int n, int m, const char *a
     if (rc != PMS_OK)
         return rc;
     ins[0].on_device = true;
+    ins[0].t = threshold_for(c, ins[0]);
     std::lock_guard<std::mutex> g(c->solve_mu);
     if (cudaSetDevice(c->device) != cudaSuccess)
         return PMS_E_CUDA;

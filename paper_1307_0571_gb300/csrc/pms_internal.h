@@ -51,6 +51,9 @@ struct DevStats {
     unsigned long long enum_nodes;
     unsigned long long leaves;
     unsigned long long raw_motifs;
+    unsigned long long cyc_filter;   // SM cycles summed over warps, per search phase
+    unsigned long long cyc_enum;
+    unsigned long long cyc_verify;
 };
 
 // Status bits a kernel raises.
@@ -82,20 +85,41 @@ cudaError_t launch_items(Layout lay, const InstDesc *d_inst, const uint64_t *d_x
                          unsigned long long *d_item_count, uint64_t item_cap,
                          int *d_status, DevStats *d_stats, cudaStream_t s);
 
+// Arguments of one search launch.
+struct SearchArgs {
+    const InstDesc *inst;
+    const void *lmers;
+    const Item *items;
+    const unsigned long long *item_count;
+    uint64_t item_cap;
+    unsigned long long *item_next;
+    uint32_t *lists;          // scratch: search_levels(t) lists of list_cap entries per warp
+    uint64_t list_cap;
+    uint64_t *keys;
+    unsigned long long *key_count;
+    uint64_t key_cap;
+    int *status;
+    DevStats *stats;
+    int key_shift;
+    int multi;
+    LaunchCfg cfg;
+    unsigned char *fscr;      // scratch: frontier-enumeration tables and levels per warp
+    uint64_t fscr_stride;     // bytes per warp (search_frontier_bytes(lay, lmax))
+    int lmax;                 // longest l in the batch
+};
+
+// Lists each search warp keeps for threshold t (levels 2..t-1, at least one).
+inline int search_levels(int t) { return t > 2 ? t - 2 : 1; }
+
 // The stack search + enumeration + verification (Algorithm 2 with Algorithm 1),
-// persistent over the item list.  Each warp owns `levels` lists of list_cap entries in
-// d_lists (scratch, levels * list_cap * 4 bytes per resident warp).
-cudaError_t launch_search(Layout lay, const InstDesc *d_inst, const void *d_lmers,
-                          const Item *d_items, const unsigned long long *d_item_count,
-                          uint64_t item_cap, unsigned long long *d_item_next, uint32_t *d_lists,
-                          uint64_t list_cap, uint64_t *d_keys,
-                          unsigned long long *d_key_count, uint64_t key_cap, int *d_status,
-                          DevStats *d_stats, const LaunchCfg &cfg, int key_shift, int multi,
-                          int levels, cudaStream_t s);
+// persistent over the item list, for plane layout `lay` and threshold t (2..kTMax).
+cudaError_t launch_search(Layout lay, int t, const SearchArgs &a, cudaStream_t s);
 
 // Resident search blocks per SM for a block of `warps_per_block` warps.
-int search_max_blocks(Layout lay, int warps_per_block);
-size_t search_smem_bytes(Layout lay, int warps_per_block);
+int search_max_blocks(Layout lay, int t, int warps_per_block);
+
+// Frontier-enumeration scratch bytes per warp for l-mers up to lmax letters.
+size_t search_frontier_bytes(Layout lay, int lmax);
 
 // ---- sort / unique / decode (pms_sort.cu) ----
 struct SortScratch {

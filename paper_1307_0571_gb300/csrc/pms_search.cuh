@@ -1,0 +1,965 @@
+// The stack search of PMS8 (Algorithm 2) with neighbourhood enumeration (Algorithm 1)
+// and verification, as one persistent kernel per plane layout and threshold T.
+//
+// Method: Section 2 (stack, filtering, threshold), Section 2.1 (sort rows by size,
+// in-place R update), Section 2.3 (subproblems), Section 2.4 (two-l-mer condition,
+// consensus distance Cd, Lemma 1, Theorem 1), Algorithms 1 and 2.
+//
+// Mapping:
+//  * A warp owns one (x, u) item at a time (x from S_1, u from the smallest row of the 2d
+//    filter) and takes the next from a global counter, so cheap and expensive items
+//    balance across the GPU.
+//  * Level k (stack size k) keeps, for each string not on the stack, the list of its
+//    surviving l-mers: one flat list per level in the warp's scratch, rows in string
+//    order, entries (string << 16 | position).  Filtering is lane-parallel over that
+//    flat list with warp-ballot compaction; per-row counts come from __match_any_sync.
+//  * The threshold T is the stack size of the pattern-driven part.  The stack is filtered
+//    up to size T-1; then every l-mer u' of the smallest remaining row closes one tuple
+//    (stack, u') whose common neighbourhood is enumerated directly, and its leaves are
+//    verified against the level-(T-1) lists.  The last filter level is skipped because it
+//    rarely empties a row and would cost more than the enumeration it saves; the result
+//    is the same, since a neighbour's witness in every row survives all necessary filters.
+//  * Enumeration: the tuples of one level node, times the subtrees below a P-letter
+//    prefix, form units that lanes take round-robin; each lane walks its unit depth first
+//    (one child test per step) and leaves go to a shared buffer verified 32 at a time.
+#pragma once
+
+#include "pms_device.cuh"
+
+namespace pms {
+namespace search {
+
+using namespace dev;
+
+template <int NB, typename W, int T>
+struct WarpSm {
+    Lm<NB, W> stk[T];
+    Lm<NB, W> cand[kCandBuf];
+    uint64_t live[T + 1];
+    int len[T + 1];
+    int brow[T + 1];
+    int bpos[T + 1];
+    int start[T + 1][kRMax];
+    int cnt[T + 1][kRMax];
+};
+
+struct WarpCounters {
+    unsigned long long tuples = 0, compares = 0, nodes = 0, leaves = 0, motifs = 0;
+    long long cyc_filter = 0, cyc_enum = 0, cyc_verify = 0;
+};
+
+template <int NB, typename W>
+struct SearchCtx {
+    const InstDesc *I;
+    int inst;
+    const Lm<NB, W> *lm;      // this instance's l-mer table
+    uint32_t *lists;          // this warp's lists; level k at (k-2)*list_cap
+    uint64_t list_cap;
+    unsigned char *fscr;      // this warp's frontier-enumeration scratch
+    int lmax;                 // longest l of the batch (sizes fscr's table)
+    uint64_t *keys;
+    unsigned long long *key_count;
+    uint64_t key_cap;
+    int *status;
+    int key_shift;
+    int multi;
+};
+
+// Row with the fewest survivors at level k (Section 2.1 "Sort rows by size": the next
+// stack element comes from the smallest row).  Ties go to the lower string index.
+template <int NB, typename W, int T>
+__device__ __forceinline__ int choose_branch(const WarpSm<NB, W, T> &S, int k, int lane)
+{
+    const uint64_t live = S.live[k];
+    unsigned a = ((live >> lane) & 1) ? ((unsigned)S.cnt[k][lane] << 6 | lane) : 0xFFFFFFFFu;
+    unsigned b = ((live >> (lane + 32)) & 1) ? ((unsigned)S.cnt[k][lane + 32] << 6 | (lane + 32))
+                                             : 0xFFFFFFFFu;
+    unsigned m = __reduce_min_sync(kFull, a < b ? a : b);
+    return (int)(m & 63);
+}
+
+// Segment starts of level k from its per-row counts (rows keep string order).
+template <int NB, typename W, int T>
+__device__ __forceinline__ void row_starts(WarpSm<NB, W, T> &S, int k, int lane)
+{
+    const uint64_t live = S.live[k];
+    int c0 = ((live >> lane) & 1) ? S.cnt[k][lane] : 0;
+    int c1 = ((live >> (lane + 32)) & 1) ? S.cnt[k][lane + 32] : 0;
+    int s0 = c0, s1 = c1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t0 = __shfl_up_sync(kFull, s0, o);
+        int t1 = __shfl_up_sync(kFull, s1, o);
+        if (lane >= o) {
+            s0 += t0;
+            s1 += t1;
+        }
+    }
+    int tot0 = __shfl_sync(kFull, s0, 31);
+    S.start[k][lane] = s0 - c0;
+    S.start[k][lane + 32] = tot0 + s1 - c1;
+    __syncwarp();
+}
+
+// Level 2 straight from the strings: stack (x, u); v of string r survives when
+// Hd(x,v) <= 2d, Hd(u,v) <= 2d and Cd(x,u,v) <= 3d (Theorem 1 with budgets d,d,d;
+// Hd(x,u) <= 2d holds for every item).  Returns false when a row empties.
+template <int NB, typename W, int T>
+__device__ bool build_level2(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &C, int b, int lane,
+                             WarpCounters &wc)
+{
+    const InstDesc &I = *C.I;
+    const Lm<NB, W> x = S.stk[0], u = S.stk[1];
+    const W dxu = diff(x, u);
+    const int two_d = 2 * I.d, three_d = 3 * I.d;
+    uint32_t *out = C.lists;
+    int len = 0;
+    uint64_t live = 0;
+    for (int r = 1; r < I.n; r++) {
+        if (r == b)
+            continue;
+        const int s0 = len;
+        const Lm<NB, W> *row = C.lm + (size_t)r * I.L;
+        for (int j0 = 0; j0 < I.L; j0 += 32) {
+            const int j = j0 + lane;
+            bool ok = false;
+            if (j < I.L) {
+                const Lm<NB, W> v = row[j];
+                const W dxv = diff(x, v), duv = diff(u, v);
+                ok = popc(dxv) <= two_d && popc(duv) <= two_d &&
+                     popc(dxu | dxv) + popc(dxu & dxv & duv) <= three_d;
+            }
+            const unsigned bal = __ballot_sync(kFull, ok);
+            if (ok)
+                out[len + __popc(bal & lanemask_lt())] = ((uint32_t)r << 16) | (uint32_t)j;
+            len += __popc(bal);
+        }
+        wc.compares += 3ull * I.L;
+        if (lane == 0)
+            S.cnt[2][r] = len - s0;
+        if (len == s0)
+            return false;
+        live |= 1ull << r;
+    }
+    if (lane == 0) {
+        S.len[2] = len;
+        S.live[2] = live;
+    }
+    __syncwarp();
+    row_starts(S, 2, lane);
+    return true;
+}
+
+// Push stk[k] (stack size becomes k+1) and filter the rows of level k other than the
+// branch row into level k+1: v survives when Hd(top,v) <= 2d and, for every earlier stack
+// l-mer s, Cd(s, top, v) <= 3d (Theorem 1 with budgets d,d,d; the pair conditions with
+// earlier l-mers hold from earlier levels).  Returns false as soon as a row empties
+// (Section 2: "If any row becomes empty ... try a different l-mer").
+template <int NB, typename W, int T>
+__device__ bool filter_level(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &C, int k, int lane,
+                             WarpCounters &wc)
+{
+    const InstDesc &I = *C.I;
+    const int two_d = 2 * I.d, three_d = 3 * I.d;
+    const Lm<NB, W> top = S.stk[k];
+    Lm<NB, W> st[T];
+    W dst[T];
+#pragma unroll
+    for (int i = 0; i < T; i++) {
+        if (i < k) {
+            st[i] = S.stk[i];
+            dst[i] = diff(st[i], top);
+        }
+    }
+    const uint32_t *in = C.lists + (size_t)(k - 2) * C.list_cap;
+    uint32_t *out = C.lists + (size_t)(k - 1) * C.list_cap;
+    const int br = S.brow[k];
+    const int bs = S.start[k][br], bc = S.cnt[k][br];
+    const int total = S.len[k] - bc;
+    const uint64_t live1 = S.live[k] & ~(1ull << br);
+    S.cnt[k + 1][lane] = 0;
+    S.cnt[k + 1][lane + 32] = 0;
+    __syncwarp();
+    int len = 0;
+    for (int c0 = 0; c0 < total; c0 += 32) {
+        const int vi = c0 + lane;
+        const bool valid = vi < total;
+        const int idx = vi < bs ? vi : vi + bc;
+        bool ok = false;
+        int row = -1;
+        uint32_t e = 0;
+        if (valid) {
+            e = in[idx];
+            row = (int)(e >> 16);
+            const Lm<NB, W> v = C.lm[(size_t)row * I.L + (e & 0xFFFF)];
+            const W dtv = diff(top, v);
+            ok = popc(dtv) <= two_d;
+#pragma unroll
+            for (int i = 0; i < T; i++) {
+                if (i < k) {
+                    const W div = diff(st[i], v);
+                    ok = ok && (popc(dst[i] | div) + popc(dst[i] & div & dtv) <= three_d);
+                }
+            }
+        }
+        const unsigned bal = __ballot_sync(kFull, ok);
+        if (ok)
+            out[len + __popc(bal & lanemask_lt())] = e;
+        len += __popc(bal);
+        const unsigned grp = __match_any_sync(kFull, row);
+        if (valid && lane == __ffs(grp) - 1)
+            S.cnt[k + 1][row] += __popc(grp & bal);
+        __syncwarp();
+        const bool last = valid && idx == S.start[k][row] + S.cnt[k][row] - 1;
+        if (__any_sync(kFull, last && S.cnt[k + 1][row] == 0)) {
+            wc.compares += (unsigned long long)(c0 + 32) * (k + 1);
+            return false;
+        }
+    }
+    wc.compares += (unsigned long long)total * (k + 1);
+    if (lane == 0) {
+        S.len[k + 1] = len;
+        S.live[k + 1] = live1;
+    }
+    __syncwarp();
+    row_starts(S, k + 1, lane);
+    return true;
+}
+
+// prune(T, r) of Algorithm 1 for a prefix of length q (positions [0, q) fixed in M), for
+// the tuple st[0..tk-1]: every budget r_i = d - Hd(M[0..q), st_i[0..q)) stays >= 0, every
+// pair keeps Hd(st_i[q..], st_j[q..]) <= r_i + r_j (two-l-mer condition, Section 2.4),
+// and every triple keeps Cd(st_i[q..], st_j[q..], st_h[q..]) <= r_i + r_j + r_h (Lemma 1;
+// with the pair conditions this is Theorem 1, exact for three l-mers).
+template <int NB, typename W, int T>
+__device__ __forceinline__ bool node_ok(const Lm<NB, W> &M, int q, int tk, int d, W lmask,
+                                        const Lm<NB, W> (&st)[T], const W (&dp)[T][T])
+{
+    const W pre = low_mask<W>(q);
+    const W suf = lmask & ~pre;
+    int e[T];
+    bool ok = true;
+#pragma unroll
+    for (int i = 0; i < T; i++) {
+        if (i < tk) {
+            e[i] = popc(diff(M, st[i]) & pre);
+            ok = ok && e[i] <= d;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < T; i++) {
+#pragma unroll
+        for (int j = i + 1; j < T; j++) {
+            if (j < tk)
+                ok = ok && (e[i] + e[j] + popc(dp[i][j] & suf) <= 2 * d);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < T; i++) {
+#pragma unroll
+        for (int j = i + 1; j < T; j++) {
+#pragma unroll
+            for (int h = j + 1; h < T; h++) {
+                if (h < tk) {
+                    const W a = dp[i][j], b = dp[i][h], c = dp[j][h];
+                    const int cd = popc((a | b) & suf) + popc(a & b & c & suf);
+                    ok = ok && (e[i] + e[j] + e[h] + cd <= 3 * d);
+                }
+            }
+        }
+    }
+    return ok;
+}
+
+// The 128-bit output key of motif M: letter codes most significant first in the low
+// l*kbits bits, the instance id above bit `key_shift` for batches.
+template <int NB, typename W>
+__device__ __forceinline__ void motif_key(const Lm<NB, W> &M, int l, int kbits, uint64_t inst,
+                                          int key_shift, int multi, uint64_t &hi, uint64_t &lo)
+{
+    hi = 0;
+    lo = 0;
+    for (int p = 0; p < l; p++) {
+        const uint64_t c = (uint64_t)get_letter(M, p);
+        hi = (hi << kbits) | (lo >> (64 - kbits));
+        lo = (lo << kbits) | c;
+    }
+    if (multi) {
+        if (key_shift >= 64)
+            hi |= inst << (key_shift - 64);
+        else {
+            lo |= inst << key_shift;
+            if (key_shift > 64 - kInstBits)
+                hi |= inst >> (64 - key_shift);
+        }
+    }
+}
+
+// isMotif(M, R') of Algorithm 2 for up to 32 buffered leaves (one per lane): every row in
+// `rows` must hold an l-mer of the level-k list within d of M.  Rows of the tuple are
+// satisfied by construction, and an l-mer within d of a common neighbour of the stack
+// survives every necessary filter, so scanning the lists equals scanning whole strings.
+template <int NB, typename W, int T>
+__device__ void verify_and_emit(const WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &C, int k,
+                                uint64_t rows, int ncand, int lane, WarpCounters &wc)
+{
+    const long long c_start = clock64();
+    const InstDesc &I = *C.I;
+    const Lm<NB, W> M = S.cand[lane < ncand ? lane : 0];
+    bool alive = lane < ncand;
+    const uint32_t *list = k >= 2 ? C.lists + (size_t)(k - 2) * C.list_cap : C.lists;
+    while (rows && __any_sync(kFull, alive)) {
+        const int r = __ffsll((long long)rows) - 1;
+        rows &= rows - 1;
+        const int s0 = S.start[k][r], c = S.cnt[k][r];
+        const Lm<NB, W> *row = C.lm + (size_t)r * I.L;
+        bool hit = false;
+        const int nalive = __popc(__ballot_sync(kFull, alive));
+        for (int j0 = 0; j0 < c; j0 += 32) {
+            const Lm<NB, W> vj = row[j0 + lane < c ? (list[s0 + j0 + lane] & 0xFFFF) : 0];
+            const int jn = c - j0 < 32 ? c - j0 : 32;
+            for (int jj = 0; jj < jn; jj++) {
+                const Lm<NB, W> v = shfl_lm(vj, jj);
+                hit = hit || popc(diff(M, v)) <= I.d;
+            }
+            wc.compares += (unsigned long long)jn * nalive;
+            if (__all_sync(kFull, hit || !alive))
+                break;
+        }
+        alive = alive && hit;
+    }
+    const unsigned bal = __ballot_sync(kFull, alive);
+    if (bal) {
+        unsigned long long base = 0;
+        if (lane == 0)
+            base = atomicAdd(C.key_count, (unsigned long long)__popc(bal));
+        base = __shfl_sync(kFull, base, 0);
+        wc.motifs += __popc(bal);
+        if (alive) {
+            const unsigned long long pos = base + __popc(bal & lanemask_lt());
+            if (pos < C.key_cap) {
+                uint64_t hi, lo;
+                motif_key(M, I.l, I.kbits, (uint64_t)C.inst, C.key_shift, C.multi, hi, lo);
+                C.keys[2 * pos] = hi;
+                C.keys[2 * pos + 1] = lo;
+            } else {
+                atomicOr(C.status, kErrKeysOverflow);
+            }
+        }
+    }
+    wc.cyc_verify += clock64() - c_start;
+}
+
+// GenerateNeighborhood (Algorithm 1) followed by isMotif on every leaf.
+//  br < 0:  one tuple, the stack stk[0..k-1]; verify against the live rows of level k.
+//  br >= 0: k == T-1 and every l-mer u' in the branch row br of level k closes the tuple
+//           (stk[0..k-1], u'); verify against the live rows of level k except br.
+template <int NB, typename W, int T>
+__device__ void enumerate(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &C, int k, int br,
+                          int lane, WarpCounters &wc)
+{
+    const long long c_start = clock64();
+    const long long v_before = wc.cyc_verify;
+    const InstDesc &I = *C.I;
+    const int l = I.l, d = I.d, K = I.k;
+    const W lmask = low_mask<W>(l);
+    const bool branch = br >= 0;
+    const int tk = branch ? k + 1 : k;
+    const uint64_t rows = branch ? (S.live[k] & ~(1ull << br)) : S.live[k];
+    Lm<NB, W> st[T];
+    W dp[T][T];
+#pragma unroll
+    for (int i = 0; i < T; i++)
+        if (i < k)
+            st[i] = S.stk[i];
+#pragma unroll
+    for (int i = 0; i < T; i++)
+#pragma unroll
+        for (int j = i + 1; j < T; j++)
+            if (j < k)
+                dp[i][j] = diff(st[i], st[j]);
+
+    const int B = branch ? S.cnt[k][br] : 1;
+    const uint32_t *blist = branch ? C.lists + (size_t)(k - 2) * C.list_cap + S.start[k][br]
+                                   : C.lists;
+    const Lm<NB, W> *brow_lm = C.lm + (size_t)(branch ? br : 0) * I.L;
+    int P = 0, U = 1;
+    while (P < l && B * U < 64) {
+        P++;
+        U *= K;
+    }
+    const int nunits = B * U;
+    wc.tuples += B;
+
+    int ncand = 0;
+    int unit = lane - 32;
+    bool have = false;
+    int q = 0, a = 0;
+    Lm<NB, W> M;
+#pragma unroll
+    for (int b = 0; b < NB; b++)
+        M.p[b] = 0;
+    unsigned long long nodes = 0;
+    for (;;) {
+        // Pick this lane's next node: the next sibling, after backtracking as far as
+        // needed, or the root of the next unit.  Every lane then tests one node.
+        if (have) {
+            while (a == K) {
+                q--;
+                if (q < P) {
+                    have = false;
+                    break;
+                }
+                a = get_letter(M, q) + 1;
+            }
+        }
+        bool fresh = false;
+        if (!have) {
+            unit += 32;
+            if (unit < nunits) {
+                const int tb = unit / U;
+                int code = unit - tb * U;
+                if (branch) {
+                    st[T - 1] = brow_lm[blist[tb] & 0xFFFF];
+#pragma unroll
+                    for (int i = 0; i < T - 1; i++)
+                        dp[i][T - 1] = diff(st[i], st[T - 1]);
+                }
+                for (int p = P - 1; p >= 0; p--) {
+                    set_letter(M, p, code % K);
+                    code /= K;
+                }
+                fresh = true;
+            }
+        } else {
+            set_letter(M, q, a);
+            a++;
+        }
+        const bool active = have || fresh;
+        const int qt = fresh ? P : q + 1;
+        bool leaf = false;
+        if (active) {
+            nodes++;
+            if (node_ok<NB, W, T>(M, qt, tk, d, lmask, st, dp)) {
+                if (qt == l)
+                    leaf = true;
+                else {
+                    have = true;
+                    q = qt;
+                    a = 0;
+                }
+            }
+        }
+        const unsigned lb = __ballot_sync(kFull, leaf);
+        if (leaf)
+            S.cand[ncand + __popc(lb & lanemask_lt())] = M;
+        ncand += __popc(lb);
+        wc.leaves += __popc(lb);
+        __syncwarp();
+        if (ncand >= 32) {
+            verify_and_emit(S, C, k, rows, 32, lane, wc);
+            __syncwarp();
+            const Lm<NB, W> rest = S.cand[32 + (lane < ncand - 32 ? lane : 0)];
+            __syncwarp();
+            if (lane < ncand - 32)
+                S.cand[lane] = rest;
+            ncand -= 32;
+            __syncwarp();
+        }
+        if (!__any_sync(kFull, have || unit + 32 < nunits))
+            break;
+    }
+    if (ncand > 0)
+        verify_and_emit(S, C, k, rows, ncand, lane, wc);
+    __syncwarp();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        nodes += __shfl_xor_sync(kFull, nodes, o);
+    wc.nodes += nodes;
+    wc.cyc_enum += (clock64() - c_start) - (wc.cyc_verify - v_before);
+}
+
+// ---------------------------------------------------------------------------------
+// Frontier form of Algorithm 1 for tuples of at most four l-mers (T <= 4, d <= 41).
+//
+// Budgets travel with each tree node as packed bytes e (byte i = mismatches so far with
+// tuple l-mer i).  With rotations of e inside the tuple, one 32-bit add forms every pair
+// sum (bytes e_i + e_{i+1}, e_i + e_{i+2}) and every triple sum (e_i + e_{i+1} + e_{i+2}),
+// and a borrow-free byte compare tests them all against per-position limits at once:
+//   e_i <= d,   e_i + e_j <= 2d - Hd(T_i[q..], T_j[q..]),
+//   e_i + e_j + e_h <= 3d - Cd(T_i[q..], T_j[q..], T_h[q..])
+// which is prune(T, r) of Algorithm 1 with r_i = d - e_i: the two-l-mer condition and
+// Lemma 1 on the suffix (Theorem 1 for three l-mers, Section 2.4).  The limits depend
+// only on the tuple and the prefix length q, so they are tabulated once per tuple.
+//
+// Nodes are expanded a chunk at a time from the deepest non-empty level (so the level
+// below is always empty and each level holds at most kFrontCap nodes); every lane tests
+// one (node, letter) child.
+
+constexpr int kTupleRound = 32;   // tuples enumerated together
+constexpr int kFrontCap = 32;     // nodes per frontier level
+
+template <int NB, typename W>
+struct FNode {
+    Lm<NB, W> M;                  // prefix (positions below the node's level)
+    uint32_t e;                   // packed mismatch counts
+    uint32_t b;                   // tuple index within the round
+};
+
+template <int NB, typename W>
+__host__ __device__ constexpr size_t frontier_scratch_bytes(int lmax)
+{
+    return (size_t)kTupleRound * (lmax + 1) * sizeof(uint4) +
+           (size_t)lmax * kFrontCap * sizeof(FNode<NB, W>);
+}
+
+// Any byte of s greater than the same byte of lim (all bytes below 128).
+__device__ __forceinline__ bool bytes_gt(uint32_t s, uint32_t lim)
+{
+    return (((lim | 0x80808080u) - s) & 0x80808080u) != 0x80808080u;
+}
+
+// Byte-permute selectors rotating the first tk bytes by one and by two places (other
+// bytes read as zero).
+__device__ __forceinline__ void rot_selectors(int tk, uint32_t &r1, uint32_t &r2)
+{
+    r1 = tk == 4 ? 0x0321u : tk == 3 ? 0x4021u : tk == 2 ? 0x4401u : 0x4444u;
+    r2 = tk == 4 ? 0x1032u : tk == 3 ? 0x4102u : 0x4444u;
+}
+
+// Limits of one tuple for prefix length q = l down to 0, and the letters of its l-mers
+// at each position: tbl[q] = {letters at q, pair limits (i,i+1), pair limits (i,i+2),
+// triple limits (i,i+1,i+2)}.  Returns false when the tuple itself fails the pair or
+// triple condition (no common neighbour, Theorem 1).
+template <int NB, typename W, int T>
+__device__ bool tuple_table(const Lm<NB, W> (&st)[T], int tk, int l, int d, uint4 *tbl)
+{
+    W dp[T][T];
+#pragma unroll
+    for (int i = 0; i < T; i++)
+#pragma unroll
+        for (int j = i + 1; j < T; j++)
+            if (j < tk)
+                dp[i][j] = diff(st[i], st[j]);
+    int hs1[T], hs2[T], cs[T];
+#pragma unroll
+    for (int i = 0; i < T; i++)
+        hs1[i] = hs2[i] = cs[i] = 0;
+    bool ok = true;
+    for (int q = l; q >= 0; q--) {
+        if (q < l) {
+#pragma unroll
+            for (int i = 0; i < T; i++) {
+                if (i < tk && tk >= 2) {
+                    const int j = (i + 1) % tk;
+                    const W dij = i < j ? dp[i][j] : dp[j][i];
+                    hs1[i] += (int)((dij >> q) & 1);
+                }
+                if (i < tk && tk == 4) {
+                    const int j = (i + 2) % 4;
+                    const W dij = i < j ? dp[i][j] : dp[j][i];
+                    hs2[i] += (int)((dij >> q) & 1);
+                }
+                if (i < tk && tk >= 3) {
+                    int a = i, b = (i + 1) % tk, c = (i + 2) % tk;
+                    // sort (a, b, c) so the pair masks come from the upper triangle
+                    if (a > b) { int t0 = a; a = b; b = t0; }
+                    if (b > c) { int t0 = b; b = c; c = t0; }
+                    if (a > b) { int t0 = a; a = b; b = t0; }
+                    const W x = dp[a][b], y = dp[a][c], z = dp[b][c];
+                    cs[i] += (int)(((x | y) >> q) & 1) + (int)(((x & y & z) >> q) & 1);
+                }
+            }
+        }
+        uint32_t lim1 = 0x7F7F7F7Fu, lim2 = 0x7F7F7F7Fu, lim3 = 0x7F7F7F7Fu, codes = 0;
+#pragma unroll
+        for (int i = 0; i < T; i++) {
+            if (i < tk) {
+                const int sh = 8 * i;
+                if (tk >= 2) {
+                    const int v = 2 * d - hs1[i];
+                    ok = ok && v >= 0;
+                    lim1 = (lim1 & ~(0xFFu << sh)) | ((uint32_t)(v < 0 ? 0 : v) << sh);
+                }
+                if (tk == 4) {
+                    const int v = 2 * d - hs2[i];
+                    ok = ok && v >= 0;
+                    lim2 = (lim2 & ~(0xFFu << sh)) | ((uint32_t)(v < 0 ? 0 : v) << sh);
+                }
+                if (tk >= 3) {
+                    const int v = 3 * d - cs[i];
+                    ok = ok && v >= 0;
+                    lim3 = (lim3 & ~(0xFFu << sh)) | ((uint32_t)(v < 0 ? 0 : v) << sh);
+                }
+                if (q < l)
+                    codes |= (uint32_t)get_letter(st[i], q) << sh;
+            }
+        }
+        tbl[q] = make_uint4(codes, lim1, lim2, lim3);
+    }
+    return ok;
+}
+
+// Algorithm 1 + isMotif for up to four l-mers per tuple; arguments as in enumerate().
+template <int NB, typename W, int T>
+__device__ void enumerate_frontier(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &C, int k,
+                                   int br, int lane, WarpCounters &wc)
+{
+    static_assert(T <= 4, "the packed-byte frontier holds at most four budgets");
+    const long long c_start = clock64();
+    const long long v_before = wc.cyc_verify;
+    const InstDesc &I = *C.I;
+    const int l = I.l, d = I.d, K = I.k;
+    const bool branch = br >= 0;
+    const int tk = branch ? k + 1 : k;
+    const uint64_t rows = branch ? (S.live[k] & ~(1ull << br)) : S.live[k];
+    uint4 *const tbl_all = reinterpret_cast<uint4 *>(C.fscr);
+    FNode<NB, W> *const front = reinterpret_cast<FNode<NB, W> *>(
+        C.fscr + (size_t)kTupleRound * (C.lmax + 1) * sizeof(uint4));
+    const int B = branch ? S.cnt[k][br] : 1;
+    const uint32_t *blist = branch ? C.lists + (size_t)(k - 2) * C.list_cap + S.start[k][br]
+                                   : C.lists;
+    const Lm<NB, W> *brow_lm = C.lm + (size_t)(branch ? br : 0) * I.L;
+
+    uint32_t r1, r2;
+    rot_selectors(tk, r1, r2);
+    uint32_t lim0 = 0x7F7F7F7Fu, used = 0;
+    for (int i = 0; i < tk; i++) {
+        lim0 = (lim0 & ~(0xFFu << (8 * i))) | ((uint32_t)d << (8 * i));
+        used |= 1u << (8 * i);
+    }
+    const int chunk = K >= 32 ? 1 : 32 / K;   // nodes expanded per step
+    const int my_node = lane / K, my_alpha = lane - (lane / K) * K;
+    const uint32_t alpha_rep = (uint32_t)my_alpha * 0x01010101u;
+    wc.tuples += B;
+    unsigned long long nodes = 0;
+    int ncand = 0;
+
+    for (int base = 0; base < B; base += kTupleRound) {
+        const int nb = B - base < kTupleRound ? B - base : kTupleRound;
+        // per-tuple tables, one tuple per lane
+        bool root_ok = false;
+        if (lane < nb) {
+            Lm<NB, W> st[T];
+#pragma unroll
+            for (int i = 0; i < T; i++)
+                if (i < k)
+                    st[i] = S.stk[i];
+            if (branch)
+                st[T - 1] = brow_lm[blist[base + lane] & 0xFFFF];
+            root_ok = tuple_table<NB, W, T>(st, tk, l, d, tbl_all + (size_t)lane * (l + 1));
+        }
+        __syncwarp();
+        // roots: empty prefix, no mismatches
+        unsigned bal = __ballot_sync(kFull, root_ok);
+        if (root_ok) {
+            FNode<NB, W> nd;
+#pragma unroll
+            for (int b2 = 0; b2 < NB; b2++)
+                nd.M.p[b2] = 0;
+            nd.e = 0;
+            nd.b = (uint32_t)lane;
+            front[__popc(bal & lanemask_lt())] = nd;
+        }
+        // lane i keeps the node counts of levels i and i + 32
+        int cnt_lo = lane == 0 ? __popc(bal) : 0, cnt_hi = 0;
+        int deepest = __popc(bal) ? 0 : -1;
+        __syncwarp();
+        while (deepest >= 0) {
+            const int p = deepest;
+            const int have = __shfl_sync(kFull, p < 32 ? cnt_lo : cnt_hi, p & 31);
+            if (have == 0) {
+                deepest--;
+                continue;
+            }
+            const int c = have < chunk ? have : chunk;
+            const int first = have - c;
+            if (lane == (p & 31)) {
+                if (p < 32)
+                    cnt_lo = first;
+                else
+                    cnt_hi = first;
+            }
+            bool ok = false;
+            FNode<NB, W> child;
+            if (my_node < c) {
+                const FNode<NB, W> nd = front[(size_t)p * kFrontCap + first + my_node];
+                const uint4 *tb = tbl_all + (size_t)nd.b * (l + 1);
+                const uint32_t codes = tb[p].x;
+                const uint4 lim = tb[p + 1];
+                const uint32_t x = codes ^ alpha_rep;
+                const uint32_t inc =
+                    (((((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x) & 0x80808080u) >> 7) & used;
+                const uint32_t e = nd.e + inc;
+                const uint32_t s1 = e + __byte_perm(e, 0, r1);
+                const uint32_t s2 = e + __byte_perm(e, 0, r2);
+                const uint32_t s3 = s1 + __byte_perm(e, 0, r2);
+                ok = !(bytes_gt(e, lim0) | bytes_gt(s1, lim.y) | bytes_gt(s2, lim.z) |
+                       bytes_gt(s3, lim.w));
+                child.M = nd.M;
+                set_letter(child.M, p, my_alpha);
+                child.e = e;
+                child.b = nd.b;
+                nodes++;
+            }
+            const unsigned okb = __ballot_sync(kFull, ok);
+            if (p + 1 == l) {
+                if (ok)
+                    S.cand[ncand + __popc(okb & lanemask_lt())] = child.M;
+                ncand += __popc(okb);
+                wc.leaves += __popc(okb);
+                __syncwarp();
+                if (ncand >= 32) {
+                    verify_and_emit(S, C, k, rows, 32, lane, wc);
+                    __syncwarp();
+                    const Lm<NB, W> rest = S.cand[32 + (lane < ncand - 32 ? lane : 0)];
+                    __syncwarp();
+                    if (lane < ncand - 32)
+                        S.cand[lane] = rest;
+                    ncand -= 32;
+                    __syncwarp();
+                }
+            } else if (okb) {
+                // the level below is empty: its nodes start at 0
+                if (ok)
+                    front[(size_t)(p + 1) * kFrontCap + __popc(okb & lanemask_lt())] = child;
+                if (lane == ((p + 1) & 31)) {
+                    if (p + 1 < 32)
+                        cnt_lo = __popc(okb);
+                    else
+                        cnt_hi = __popc(okb);
+                }
+                deepest = p + 1;
+                __syncwarp();
+            }
+        }
+    }
+    if (ncand > 0)
+        verify_and_emit(S, C, k, rows, ncand, lane, wc);
+    __syncwarp();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        nodes += __shfl_xor_sync(kFull, nodes, o);
+    wc.nodes += nodes;
+    wc.cyc_enum += (clock64() - c_start) - (wc.cyc_verify - v_before);
+}
+
+// Enumeration entry: the frontier form for T <= 4 (the host sends instances with
+// d > 41 to T >= 5), the per-lane walk otherwise.
+template <int NB, typename W, int T>
+__device__ __forceinline__ void enumerate_any(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &C,
+                                              int k, int br, int lane, WarpCounters &wc)
+{
+    if constexpr (T <= 4)
+        enumerate_frontier(S, C, k, br, lane, wc);
+    else
+        enumerate(S, C, k, br, lane, wc);
+}
+
+// One (x, u) item: Algorithm 2 from stack size 2, with an explicit stack of levels.
+template <int NB, typename W, int T>
+__device__ void run_item(WarpSm<NB, W, T> &S, SearchCtx<NB, W> &C, const Item &it, int lane,
+                         WarpCounters &wc)
+{
+    const InstDesc &I = *C.I;
+    if (lane == 0)
+        S.stk[0] = C.lm[it.x];
+    if (it.b == 0xFFFF) {  // one string: the d-neighbourhood of x is the answer
+        if (lane == 0)
+            S.live[1] = 0;
+        __syncwarp();
+        enumerate_any(S, C, 1, -1, lane, wc);
+        return;
+    }
+    if (lane == 0)
+        S.stk[1] = C.lm[(size_t)it.b * I.L + it.u];
+    __syncwarp();
+    long long c0 = clock64();
+    const bool alive = build_level2(S, C, it.b, lane, wc);
+    wc.cyc_filter += clock64() - c0;
+    if (!alive)
+        return;
+    if (T == 2 || S.live[2] == 0) {
+        enumerate_any(S, C, 2, -1, lane, wc);
+        return;
+    }
+    if (T == 3) {
+        enumerate_any(S, C, 2, choose_branch(S, 2, lane), lane, wc);
+        return;
+    }
+    int k = 2;
+    {
+        const int b2 = choose_branch(S, 2, lane);
+        if (lane == 0) {
+            S.brow[2] = b2;
+            S.bpos[2] = 0;
+        }
+        __syncwarp();
+    }
+    for (;;) {
+        // invariant: k < T-1 and the branch row of level k is chosen
+        const int br = S.brow[k];
+        const int pos = S.bpos[k];
+        if (pos >= S.cnt[k][br]) {
+            if (k == 2)
+                return;
+            k--;
+            continue;
+        }
+        const uint32_t e = C.lists[(size_t)(k - 2) * C.list_cap + S.start[k][br] + pos];
+        __syncwarp();
+        if (lane == 0) {
+            S.bpos[k] = pos + 1;
+            S.stk[k] = C.lm[(size_t)(e >> 16) * I.L + (e & 0xFFFF)];
+        }
+        __syncwarp();
+        c0 = clock64();
+        const bool ok = filter_level(S, C, k, lane, wc);
+        wc.cyc_filter += clock64() - c0;
+        if (!ok)
+            continue;
+        const int k1 = k + 1;
+        if (S.live[k1] == 0) {
+            enumerate_any(S, C, k1, -1, lane, wc);
+        } else if (k1 == T - 1) {
+            enumerate_any(S, C, k1, choose_branch(S, k1, lane), lane, wc);
+        } else {
+            k = k1;
+            const int nb = choose_branch(S, k, lane);
+            if (lane == 0) {
+                S.brow[k] = nb;
+                S.bpos[k] = 0;
+            }
+            __syncwarp();
+        }
+    }
+}
+
+template <int NB, typename W, int T>
+__global__ void __launch_bounds__(128) search_kernel(
+    const InstDesc *__restrict__ inst, const Lm<NB, W> *__restrict__ lmers,
+    const Item *__restrict__ items, const unsigned long long *item_count, uint64_t item_cap,
+    unsigned long long *item_next, uint32_t *lists, uint64_t list_cap, uint64_t *keys,
+    unsigned long long *key_count, uint64_t key_cap, int *status, DevStats *stats,
+    int key_shift, int multi, unsigned char *fscr, uint64_t fscr_stride, int lmax)
+{
+    extern __shared__ unsigned char smem_raw[];
+    WarpSm<NB, W, T> &S = reinterpret_cast<WarpSm<NB, W, T> *>(smem_raw)[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    constexpr int levels = T > 2 ? T - 2 : 1;
+    SearchCtx<NB, W> C;
+    C.lists = lists + gw * (uint64_t)levels * list_cap;
+    C.list_cap = list_cap;
+    C.fscr = fscr + gw * fscr_stride;
+    C.lmax = lmax;
+    C.keys = keys;
+    C.key_count = key_count;
+    C.key_cap = key_cap;
+    C.status = status;
+    C.key_shift = key_shift;
+    C.multi = multi;
+    WarpCounters wc;
+    unsigned long long done = 0;
+    const unsigned long long nitems = *item_count < item_cap ? *item_count : item_cap;
+    for (;;) {
+        unsigned long long it = 0;
+        if (lane == 0)
+            it = atomicAdd(item_next, 1ull);
+        it = __shfl_sync(kFull, it, 0);
+        if (it >= nitems)
+            break;
+        const Item item = items[it];
+        C.I = inst + item.inst;
+        C.inst = (int)item.inst;
+        C.lm = lmers + C.I->lmer_off;
+        run_item(S, C, item, lane, wc);
+        done++;
+        __syncwarp();
+    }
+    if (lane == 0) {
+        atomicAdd(&stats->items, done);
+        atomicAdd(&stats->tuples, wc.tuples);
+        atomicAdd(&stats->hd_compares, wc.compares);
+        atomicAdd(&stats->enum_nodes, wc.nodes);
+        atomicAdd(&stats->leaves, wc.leaves);
+        atomicAdd(&stats->raw_motifs, wc.motifs);
+        atomicAdd(&stats->cyc_filter, (unsigned long long)wc.cyc_filter);
+        atomicAdd(&stats->cyc_enum, (unsigned long long)wc.cyc_enum);
+        atomicAdd(&stats->cyc_verify, (unsigned long long)wc.cyc_verify);
+    }
+}
+
+template <int NB, typename W, int T>
+size_t smem_bytes(int wpb)
+{
+    return sizeof(WarpSm<NB, W, T>) * (size_t)wpb;
+}
+
+template <int NB, typename W, int T>
+cudaError_t launch(const SearchArgs &a, cudaStream_t s)
+{
+    const size_t smem = smem_bytes<NB, W, T>(a.cfg.warps_per_block);
+    cudaError_t e = cudaFuncSetAttribute(search_kernel<NB, W, T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    search_kernel<NB, W, T><<<a.cfg.blocks, a.cfg.warps_per_block * 32, smem, s>>>(
+        a.inst, static_cast<const Lm<NB, W> *>(a.lmers), a.items, a.item_count, a.item_cap,
+        a.item_next, a.lists, a.list_cap, a.keys, a.key_count, a.key_cap, a.status, a.stats,
+        a.key_shift, a.multi, a.fscr, a.fscr_stride, a.lmax);
+    return cudaGetLastError();
+}
+
+template <int NB, typename W, int T>
+int max_blocks(int wpb)
+{
+    int nb = 0;
+    const size_t smem = smem_bytes<NB, W, T>(wpb);
+    cudaFuncSetAttribute(search_kernel<NB, W, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, search_kernel<NB, W, T>, wpb * 32,
+                                                      smem) != cudaSuccess)
+        return 0;
+    return nb;
+}
+
+// Dispatch over the thresholds 2..kTMax for one plane layout.
+template <int NB, typename W>
+cudaError_t launch_layout(int t, const SearchArgs &a, cudaStream_t s)
+{
+    switch (t) {
+    case 2: return launch<NB, W, 2>(a, s);
+    case 3: return launch<NB, W, 3>(a, s);
+    case 4: return launch<NB, W, 4>(a, s);
+    case 5: return launch<NB, W, 5>(a, s);
+    case 6: return launch<NB, W, 6>(a, s);
+    case 7: return launch<NB, W, 7>(a, s);
+    case 8: return launch<NB, W, 8>(a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <int NB, typename W>
+int max_blocks_layout(int t, int wpb)
+{
+    switch (t) {
+    case 2: return max_blocks<NB, W, 2>(wpb);
+    case 3: return max_blocks<NB, W, 3>(wpb);
+    case 4: return max_blocks<NB, W, 4>(wpb);
+    case 5: return max_blocks<NB, W, 5>(wpb);
+    case 6: return max_blocks<NB, W, 6>(wpb);
+    case 7: return max_blocks<NB, W, 7>(wpb);
+    case 8: return max_blocks<NB, W, 8>(wpb);
+    }
+    return 0;
+}
+
+template <int NB, typename W>
+size_t fscr_layout(int lmax)
+{
+    return frontier_scratch_bytes<NB, W>(lmax);
+}
+
+}  // namespace search
+}  // namespace pms

@@ -52,7 +52,8 @@ class pms_stats(ctypes.Structure):
     _fields_ = [("items", ctypes.c_uint64), ("tuples", ctypes.c_uint64),
                 ("hd_compares", ctypes.c_uint64), ("enum_nodes", ctypes.c_uint64),
                 ("leaves", ctypes.c_uint64), ("raw_motifs", ctypes.c_uint64),
-                ("kernel_ms", ctypes.c_double), ("search_ms", ctypes.c_double),
+                ("cyc_filter", ctypes.c_uint64), ("cyc_enum", ctypes.c_uint64),
+                ("cyc_verify", ctypes.c_uint64), ("kernel_ms", ctypes.c_double), ("search_ms", ctypes.c_double),
                 ("threshold", ctypes.c_int)]
 
 
