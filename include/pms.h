@@ -92,6 +92,11 @@ typedef struct pms_stats {
     uint64_t cyc_filter;      /* search-kernel SM cycles in filtering, summed over warps */
     uint64_t cyc_enum;        /* ... in neighbourhood enumeration (Algorithm 1) */
     uint64_t cyc_verify;      /* ... in verification (isMotif) */
+    uint64_t search_ops;      /* algorithmic integer ops of the search kernel (unit costs in
+                                 the library's documentation of the roofline) */
+    uint64_t launches;        /* kernels launched by the solve */
+    uint64_t h2d_bytes;       /* bytes copied host -> device by the solve */
+    uint64_t d2h_bytes;       /* bytes copied device -> host by the solve */
     double kernel_ms;         /* device time of the whole solve (CUDA events) */
     double search_ms;         /* device time of the search kernel alone */
     int threshold;            /* threshold used */

@@ -311,6 +311,15 @@ struct BatchOut {
 int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
               const std::vector<int> &idx, pms_stats *stats_out)
 {
+    uint64_t h2d = 0, d2h = 0;
+    auto copy = [&](void *dst, const void *src, size_t bytes, cudaMemcpyKind kind,
+                    cudaStream_t st) {
+        if (kind == cudaMemcpyHostToDevice)
+            h2d += bytes;
+        else if (kind == cudaMemcpyDeviceToHost)
+            d2h += bytes;
+        return cudaMemcpyAsync(dst, src, bytes, kind, st);
+    };
     const int ninst = (int)ins.size();
     cudaStream_t s = w.stream;
     const Layout lay = ins[0].lay;
@@ -384,15 +393,15 @@ int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
         }
         uint8_t *dst = w.seqs.as<uint8_t>() + desc[i].seq_off;
         size_t bytes = (size_t)ins[i].n * ins[i].m;
-        PMS_CU(cudaMemcpyAsync(dst, ins[i].seqs, bytes,
+        PMS_CU(copy(dst, ins[i].seqs, bytes,
                                ins[i].on_device ? cudaMemcpyDeviceToDevice
                                                 : cudaMemcpyHostToDevice,
                                s));
     }
     PMS_CU(cudaEventRecord(w.ev[0], s));
-    PMS_CU(cudaMemcpyAsync(w.maps.p, maps.data(), maps.size(), cudaMemcpyHostToDevice, s));
-    PMS_CU(cudaMemcpyAsync(w.alpha.p, alpha.data(), alpha.size(), cudaMemcpyHostToDevice, s));
-    PMS_CU(cudaMemcpyAsync(w.inst.p, desc.data(), sizeof(InstDesc) * ninst,
+    PMS_CU(copy(w.maps.p, maps.data(), maps.size(), cudaMemcpyHostToDevice, s));
+    PMS_CU(copy(w.alpha.p, alpha.data(), alpha.size(), cudaMemcpyHostToDevice, s));
+    PMS_CU(copy(w.inst.p, desc.data(), sizeof(InstDesc) * ninst,
                            cudaMemcpyHostToDevice, s));
     Counters *dc = w.counters.as<Counters>();
     PMS_CU(cudaMemsetAsync(dc, 0, sizeof(Counters), s));
@@ -402,8 +411,10 @@ int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
     PMS_CU(launch_items(lay, w.inst.as<InstDesc>(), nullptr, ninst, x_total, w.lmers.p,
                         w.items.as<Item>(), &dc->item_count, item_cap, &dc->status, &dc->stats,
                         s));
+    uint64_t launches = (lmer_total ? 1 : 0) + (x_total ? 1 : 0);
     Counters hc{};
     for (int attempt = 0;; attempt++) {
+        launches++;
         PMS_CU(cudaEventRecord(w.ev[1], s));
         SearchArgs sa{w.inst.as<InstDesc>(), w.lmers.p, w.items.as<Item>(), &dc->item_count,
                       item_cap, &dc->item_next, w.lists.as<uint32_t>(), list_cap,
@@ -412,7 +423,7 @@ int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
                       lmax};
         PMS_CU(launch_search(lay, t, sa, s));
         PMS_CU(cudaEventRecord(w.ev[2], s));
-        PMS_CU(cudaMemcpyAsync(&hc, dc, sizeof hc, cudaMemcpyDeviceToHost, s));
+        PMS_CU(copy(&hc, dc, sizeof hc, cudaMemcpyDeviceToHost, s));
         PMS_CU(cudaStreamSynchronize(s));
         if (hc.status & kErrAlphabet)
             return PMS_E_ALPHABET;
@@ -430,7 +441,7 @@ int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
         if (c->budget && c->held > c->budget)
             return PMS_E_NOMEM;
         unsigned long long zero[2] = {0, 0};
-        PMS_CU(cudaMemcpyAsync(&dc->item_next, zero, 16, cudaMemcpyHostToDevice, s));
+        PMS_CU(copy(&dc->item_next, zero, 16, cudaMemcpyHostToDevice, s));
         PMS_CU(cudaMemsetAsync(&dc->status, 0, sizeof(int), s));
         PMS_CU(cudaMemsetAsync(&dc->stats, 0, sizeof(DevStats), s));
     }
@@ -446,13 +457,17 @@ int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
     size_t nuniq = 0;
     PMS_CU(sort_unique_keys(w.keys.as<uint64_t>(), nkeys, sort_bits, scr, &dc->uniq_total,
                             &nuniq, s));
+    if (nkeys) {
+        launches += 3ull * ((sort_bits + 7) / 8) + 3 + (nuniq ? 1 : 0);
+        d2h += sizeof(unsigned long long);   // the unique count read back by the sort
+    }
     PMS_CU(cudaMemsetAsync(w.first.p, 0xFF, 8 * (size_t)ninst, s));
     PMS_CU(cudaMemsetAsync(w.last.p, 0xFF, 8 * (size_t)ninst, s));
     PMS_CU(launch_ranges(w.keys.as<uint64_t>(), nuniq, key_bits, multi, ninst,
                          w.first.as<long long>(), w.last.as<long long>(), s));
     std::vector<long long> first(ninst), last(ninst);
-    PMS_CU(cudaMemcpyAsync(first.data(), w.first.p, 8 * (size_t)ninst, cudaMemcpyDeviceToHost, s));
-    PMS_CU(cudaMemcpyAsync(last.data(), w.last.p, 8 * (size_t)ninst, cudaMemcpyDeviceToHost, s));
+    PMS_CU(copy(first.data(), w.first.p, 8 * (size_t)ninst, cudaMemcpyDeviceToHost, s));
+    PMS_CU(copy(last.data(), w.last.p, 8 * (size_t)ninst, cudaMemcpyDeviceToHost, s));
     PMS_CU(cudaStreamSynchronize(s));
     std::vector<uint64_t> counts(ninst), byte_off(ninst);
     uint64_t bytes = 0;
@@ -470,8 +485,9 @@ int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
         if (counts[0] > bo.dev_cap)
             bytes = 0;   // decode nothing past the caller's capacity
     }
-    PMS_CU(cudaMemcpyAsync(w.byte_off.p, byte_off.data(), 8 * (size_t)ninst,
+    PMS_CU(copy(w.byte_off.p, byte_off.data(), 8 * (size_t)ninst,
                            cudaMemcpyHostToDevice, s));
+    launches += bytes ? 1 : 0;
     if (bytes)
         PMS_CU(launch_decode(w.keys.as<uint64_t>(), nuniq, key_bits, multi, w.inst.as<InstDesc>(),
                              w.alpha.as<uint8_t>(), out_dev, w.byte_off.as<uint64_t>(),
@@ -492,6 +508,10 @@ int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
     st.cyc_filter = hc.stats.cyc_filter;
     st.cyc_enum = hc.stats.cyc_enum;
     st.cyc_verify = hc.stats.cyc_verify;
+    st.search_ops = hc.stats.search_ops;
+    st.launches = launches;
+    st.h2d_bytes = h2d;
+    st.d2h_bytes = d2h;
     st.kernel_ms = total_ms;
     st.search_ms = search_ms;
     st.threshold = ins[0].t;
@@ -518,6 +538,7 @@ int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
                     bo.rc[idx[i]] = PMS_E_NOMEM;
                     continue;
                 }
+                d2h += nb;
                 PMS_CU(cudaMemcpy(r.motifs, out_dev + byte_off[i], nb, cudaMemcpyDeviceToHost));
             }
             r.count = counts[i];
@@ -568,6 +589,10 @@ int run_batch(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo, pm
             total.cyc_filter += st.cyc_filter;
             total.cyc_enum += st.cyc_enum;
             total.cyc_verify += st.cyc_verify;
+            total.search_ops += st.search_ops;
+            total.launches += st.launches;
+            total.h2d_bytes += st.h2d_bytes;
+            total.d2h_bytes += st.d2h_bytes;
             total.kernel_ms += st.kernel_ms;
             total.search_ms += st.search_ms;
             total.threshold = st.threshold;

@@ -54,7 +54,31 @@ struct DevStats {
     unsigned long long cyc_filter;   // SM cycles summed over warps, per search phase
     unsigned long long cyc_enum;
     unsigned long long cyc_verify;
+    unsigned long long search_ops;   // algorithmic integer ops of the search kernel
 };
+
+// Algorithmic integer-op counts per unit of work, for NB planes of 32-bit words (64-bit
+// words cost twice).  A diff (positions where two l-mers differ) is NB three-input
+// logic ops; Hd is diff + popcount + compare.
+//   Hd test                           NB + 2
+//   Theorem 1 triple, given D(s,top)  NB + 6  (diff, or, popc, and3, popc, add, compare)
+//   level-2 test (x, u, v)            2 NB + 10
+//   filter test at stack size k       NB + 2 + k (NB + 6)
+//   frontier child (packed budgets)   25 + 2 NB (letter mismatch bytes, 3 byte permutes,
+//                                     3 adds, 4 byte-wise compares, set the letter)
+//   per-lane walk node, tuple of tk   tk (NB + 3) + 5 C(tk,2) + 9 C(tk,3)
+__host__ __device__ inline unsigned long long op_hd(int nb) { return nb + 2; }
+__host__ __device__ inline unsigned long long op_level2(int nb) { return 2 * nb + 10; }
+__host__ __device__ inline unsigned long long op_filter(int nb, int k)
+{
+    return nb + 2 + (unsigned long long)k * (nb + 6);
+}
+__host__ __device__ inline unsigned long long op_child(int nb) { return 25 + 2 * nb; }
+__host__ __device__ inline unsigned long long op_walk(int nb, int tk)
+{
+    return (unsigned long long)tk * (nb + 3) + 5ull * tk * (tk - 1) / 2 +
+           9ull * tk * (tk - 1) * (tk - 2) / 6;
+}
 
 // Status bits a kernel raises.
 enum : int {

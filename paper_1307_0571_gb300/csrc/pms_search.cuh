@@ -44,9 +44,12 @@ struct WarpSm {
 };
 
 struct WarpCounters {
-    unsigned long long tuples = 0, compares = 0, nodes = 0, leaves = 0, motifs = 0;
+    unsigned long long tuples = 0, compares = 0, nodes = 0, leaves = 0, motifs = 0, ops = 0;
     long long cyc_filter = 0, cyc_enum = 0, cyc_verify = 0;
 };
+
+template <typename W>
+__device__ __forceinline__ unsigned long long wscale() { return sizeof(W) / 4; }
 
 template <int NB, typename W>
 struct SearchCtx {
@@ -135,6 +138,7 @@ __device__ bool build_level2(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &C, int
             len += __popc(bal);
         }
         wc.compares += 3ull * I.L;
+        wc.ops += (unsigned long long)I.L * op_level2(NB) * wscale<W>();
         if (lane == 0)
             S.cnt[2][r] = len - s0;
         if (len == s0)
@@ -212,11 +216,14 @@ __device__ bool filter_level(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &C, int
         __syncwarp();
         const bool last = valid && idx == S.start[k][row] + S.cnt[k][row] - 1;
         if (__any_sync(kFull, last && S.cnt[k + 1][row] == 0)) {
-            wc.compares += (unsigned long long)(c0 + 32) * (k + 1);
+            const int done = c0 + 32 < total ? c0 + 32 : total;
+            wc.compares += (unsigned long long)done * (k + 1);
+            wc.ops += (unsigned long long)done * op_filter(NB, k) * wscale<W>();
             return false;
         }
     }
     wc.compares += (unsigned long long)total * (k + 1);
+    wc.ops += (unsigned long long)total * op_filter(NB, k) * wscale<W>();
     if (lane == 0) {
         S.len[k + 1] = len;
         S.live[k + 1] = live1;
@@ -323,6 +330,7 @@ __device__ void verify_and_emit(const WarpSm<NB, W, T> &S, const SearchCtx<NB, W
                 hit = hit || popc(diff(M, v)) <= I.d;
             }
             wc.compares += (unsigned long long)jn * nalive;
+            wc.ops += (unsigned long long)jn * nalive * op_hd(NB) * wscale<W>();
             if (__all_sync(kFull, hit || !alive))
                 break;
         }
@@ -476,6 +484,7 @@ __device__ void enumerate(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &C, int k,
     for (int o = 16; o > 0; o >>= 1)
         nodes += __shfl_xor_sync(kFull, nodes, o);
     wc.nodes += nodes;
+    wc.ops += nodes * op_walk(NB, tk) * wscale<W>();
     wc.cyc_enum += (clock64() - c_start) - (wc.cyc_verify - v_before);
 }
 
@@ -741,6 +750,7 @@ __device__ void enumerate_frontier(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &
     for (int o = 16; o > 0; o >>= 1)
         nodes += __shfl_xor_sync(kFull, nodes, o);
     wc.nodes += nodes;
+    wc.ops += nodes * (25ull + 2ull * NB * wscale<W>());
     wc.cyc_enum += (clock64() - c_start) - (wc.cyc_verify - v_before);
 }
 
@@ -887,6 +897,7 @@ __global__ void __launch_bounds__(128) search_kernel(
         atomicAdd(&stats->cyc_filter, (unsigned long long)wc.cyc_filter);
         atomicAdd(&stats->cyc_enum, (unsigned long long)wc.cyc_enum);
         atomicAdd(&stats->cyc_verify, (unsigned long long)wc.cyc_verify);
+        atomicAdd(&stats->search_ops, wc.ops);
     }
 }
 

@@ -53,7 +53,10 @@ class pms_stats(ctypes.Structure):
                 ("hd_compares", ctypes.c_uint64), ("enum_nodes", ctypes.c_uint64),
                 ("leaves", ctypes.c_uint64), ("raw_motifs", ctypes.c_uint64),
                 ("cyc_filter", ctypes.c_uint64), ("cyc_enum", ctypes.c_uint64),
-                ("cyc_verify", ctypes.c_uint64), ("kernel_ms", ctypes.c_double), ("search_ms", ctypes.c_double),
+                ("cyc_verify", ctypes.c_uint64), ("search_ops", ctypes.c_uint64),
+                ("launches", ctypes.c_uint64), ("h2d_bytes", ctypes.c_uint64),
+                ("d2h_bytes", ctypes.c_uint64), ("kernel_ms", ctypes.c_double),
+                ("search_ms", ctypes.c_double),
                 ("threshold", ctypes.c_int)]
 
 
@@ -177,6 +180,16 @@ class Context:
         res = pms_result()
         rc = self.lib.pms_solve(self.h, _b(seqs), n, m, alphabet.encode("ascii"), l, d,
                                 ctypes.byref(res))
+        if rc != PMS_OK:
+            raise PMSError(rc, "pms_solve")
+        self.last_stats = pms_stats.from_buffer_copy(res.stats)
+        return _take(self.lib, res)
+
+    def solve_ptr(self, host_ptr: int, n: int, m: int, alphabet: str, l: int, d: int) -> list[str]:
+        """pms_solve on sequences at a host address (e.g. pinned memory)."""
+        res = pms_result()
+        rc = self.lib.pms_solve(self.h, ctypes.cast(ctypes.c_void_p(host_ptr), ctypes.c_char_p),
+                                n, m, alphabet.encode("ascii"), l, d, ctypes.byref(res))
         if rc != PMS_OK:
             raise PMSError(rc, "pms_solve")
         self.last_stats = pms_stats.from_buffer_copy(res.stats)
