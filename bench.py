@@ -42,9 +42,21 @@ if ROOT not in sys.path:
 
 METRIC = "solve time per (l,d) instance; l-mer Hd compares/s vs roofline; batched p99"
 UNIT = "instances/s"
-WORKLOAD = dict(l=17, d=6, n=20, m=600, alphabet="ACGT")
-WORKLOAD_NAME = "planted DNA (l,d)=(17,6), n=20, m=600 (one instance per step)"
-SEED_CONFIG = 2                  # seeds synth.workload_seed(2, j)
+# The timed workload (default dna_17_6); the others exist for profiling smaller and larger
+# cases of the same kernels.
+WORKLOADS = {
+    "dna_17_6": (dict(l=17, d=6, n=20, m=600, alphabet="ACGT"), 2),
+    "dna_13_4": (dict(l=13, d=4, n=20, m=600, alphabet="ACGT"), 1),
+    "dna_15_5": (dict(l=15, d=5, n=20, m=600, alphabet="ACGT"), 2),
+    "dna_19_7": (dict(l=19, d=7, n=20, m=600, alphabet="ACGT"), 2),
+    "dna_21_8": (dict(l=21, d=8, n=20, m=600, alphabet="ACGT"), 2),
+}
+WORKLOAD, SEED_CONFIG = WORKLOADS["dna_17_6"]   # seeds synth.workload_seed(config, j)
+
+
+def _workload_name(w):
+    return (f"planted DNA (l,d)=({w['l']},{w['d']}), n={w['n']}, m={w['m']} "
+            f"(one instance per step)")
 SM_COUNT = 152
 INT_OPS_PER_CLK_SM = 128         # 4 SMSPs x 32 lanes issue-limited integer ops
 CPU_SAMPLE_X = 24                # l-mers of S_1 in the CPU baseline sample
@@ -186,7 +198,7 @@ def run_reference(args) -> None:
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000 * total / len(times), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAME, "sample": f"{per_step} l-mers of S_1 per step",
+        "config": {"workload": _workload_name(WORKLOAD), "sample": f"{per_step} l-mers of S_1 per step",
                    "parallelism": "host threads"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"each step: PMS8 oracle on the subproblems of l-mers "
@@ -207,7 +219,7 @@ def run_ours(args) -> None:
     from paper_1307_0571_gb300 import pms, synth
     W_ = WORKLOAD
     l, d, n, m = W_["l"], W_["d"], W_["n"], W_["m"]
-    ctx = pms.Context(local)
+    ctx = pms.Context(local, threshold=args.threshold)
     total_steps = args.warmup + args.steps
     insts = [synth.planted_instance(_seed(rank, j), n, m, l, d) for j in range(total_steps)]
     dseqs = [torch.frombuffer(bytearray(i.seqs), dtype=torch.uint8).to("cuda") for i in insts]
@@ -288,7 +300,7 @@ def run_ours(args) -> None:
         "vs_baseline": None,
         "dtype": "u32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAME, "instances_per_rank": args.steps,
+        "config": {"workload": _workload_name(WORKLOAD), "instances_per_rank": args.steps,
                    "threshold": stats[0].threshold, "parallelism": f"replicas x{world}",
                    "l2": "256 MiB buffer rewritten before every step (outside the events)",
                    "inputs": "strings resident in HBM; result left in HBM"},
@@ -325,7 +337,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="dna_17_6")
+    ap.add_argument("--threshold", type=int, default=0, help="0 = autotuned")
     args = ap.parse_args()
+    global WORKLOAD, SEED_CONFIG
+    WORKLOAD, SEED_CONFIG = WORKLOADS[args.workload]
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":

@@ -152,8 +152,8 @@ void pms_result_free(pms_result *res);
 /* Static description of an error code. */
 const char *pms_strerror(int code);
 
-/* Number of instance classes (l, d, n, m, alphabet size) whose threshold the autotuner
- * has cached, and a reset of that cache. */
+/* Number of instance classes (l, d, alphabet size, and n and m rounded to powers of two)
+ * whose threshold the autotuner has cached, and a reset of that cache. */
 int pms_autotune_entries(pms_ctx *ctx);
 void pms_autotune_reset(pms_ctx *ctx);
 

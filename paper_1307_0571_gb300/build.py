@@ -29,8 +29,16 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libpms")
 
 
+def _extra_flags() -> list[str]:
+    """Extra nvcc flags from PMS_NVCC_FLAGS (e.g. -DPMS_SEARCH_MIN_BLOCKS=6), for tuning."""
+    return os.environ.get("PMS_NVCC_FLAGS", "").split()
+
+
 def _stale() -> bool:
     if not os.path.exists(LIB):
+        return True
+    stamp = LIB + ".flags"
+    if not os.path.exists(stamp) or open(stamp).read() != " ".join(_extra_flags()):
         return True
     t = os.path.getmtime(LIB)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
@@ -44,7 +52,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OUT, exist_ok=True)
     cc = nvcc()
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
-                     "-I", os.path.join(ROOT, "include"), "-I", CSRC]
+                     "-I", os.path.join(ROOT, "include"), "-I", CSRC] + _extra_flags()
 
     def compile_one(src: str) -> str:
         obj = os.path.join(OUT, src.replace(".cu", ".o"))
@@ -64,6 +72,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(LIB + ".flags", "w") as f:
+        f.write(" ".join(_extra_flags()))
     return LIB
 
 

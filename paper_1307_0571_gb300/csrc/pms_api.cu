@@ -233,7 +233,7 @@ struct pms_ctx {
     size_t budget = 0;
     Workspace main;
     std::mutex solve_mu;
-    // threshold autotuner cache: (l, d, n, m, k) -> t
+    // threshold autotuner cache: tune_key -> t
     std::mutex tune_mu;
     std::map<std::tuple<int, int, int, int, int>, int> tune;
     // serving
@@ -273,6 +273,14 @@ void ws_free(pms_ctx *c, Workspace &w)
     w.stream = nullptr;
 }
 
+// Autotuner classes: (l, d, alphabet size) and n, m rounded to the nearest power of two
+// (their effect on the best threshold is smooth; see Appendix D's cost model).
+std::tuple<int, int, int, int, int> tune_key(const Prep &p)
+{
+    return std::make_tuple(p.l, p.d, p.k, (int)std::lround(std::log2((double)p.n)),
+                           (int)std::lround(std::log2((double)p.m)));
+}
+
 // Thresholds 2..4 enumerate with packed byte budgets, which hold d <= 41.
 int threshold_for_raw(pms_ctx *c, const Prep &p);
 
@@ -289,13 +297,10 @@ int threshold_for_raw(pms_ctx *c, const Prep &p)
     if (c->opts.threshold)
         return std::max(2, std::min(c->opts.threshold, kTMax));
     std::lock_guard<std::mutex> g(c->tune_mu);
-    auto key = std::make_tuple(p.l, p.d, p.n, p.m, p.k);
-    auto it = c->tune.find(key);
+    auto it = c->tune.find(tune_key(p));
     if (it != c->tune.end())
         return it->second;
-    int t = model_threshold(p.n, p.m, p.l, p.d, p.k);
-    c->tune[key] = t;
-    return t;
+    return model_threshold(p.n, p.m, p.l, p.d, p.k);
 }
 
 struct BatchOut {
@@ -308,8 +313,16 @@ struct BatchOut {
 };
 
 // The whole pipeline for instances that share one plane layout.
+// With `tune` set, run only packing, the 2d filter and the search on a strided sample of
+// the items for every threshold in tune->cand, and report the fastest in tune->best.
+struct Tune {
+    std::vector<int> cand;
+    int best = 0;
+    std::vector<float> ms;
+};
+
 int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
-              const std::vector<int> &idx, pms_stats *stats_out)
+              const std::vector<int> &idx, pms_stats *stats_out, Tune *tune = nullptr)
 {
     uint64_t h2d = 0, d2h = 0;
     auto copy = [&](void *dst, const void *src, size_t bytes, cudaMemcpyKind kind,
@@ -355,15 +368,20 @@ int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
     const int sort_bits = key_bits + (multi ? kInstBits : 0);
     const int levels = search_levels(t);
 
-    // search launch shape
+    // search launch shape for threshold tt
     int wpb = c->opts.warps_per_block ? std::max(1, std::min(c->opts.warps_per_block, 4)) : 4;
-    int per_sm = search_max_blocks(lay, t, wpb);
-    if (per_sm <= 0)
-        return PMS_E_CUDA;
-    if (c->opts.blocks_per_sm)
-        per_sm = std::min(per_sm, c->opts.blocks_per_sm);
-    LaunchCfg cfg{wpb, per_sm * c->sm_count};
-    const uint64_t nwarps = (uint64_t)cfg.blocks * wpb;
+    auto shape = [&](int tt, LaunchCfg &cfg) {
+        int per_sm = search_max_blocks(lay, tt, wpb);
+        if (per_sm <= 0)
+            return PMS_E_CUDA;
+        if (c->opts.blocks_per_sm)
+            per_sm = std::min(per_sm, c->opts.blocks_per_sm);
+        cfg = LaunchCfg{wpb, per_sm * c->sm_count};
+        return PMS_OK;
+    };
+    LaunchCfg cfg{};
+    PMS_TRY(shape(t, cfg));
+    (void)levels;
 
     // buffers
     uint64_t key_cap = std::max<uint64_t>(1 << 16, w.keys.cap / 16);
@@ -373,9 +391,16 @@ int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
     PMS_TRY(w.inst.ensure(sizeof(InstDesc) * ninst, c->held));
     PMS_TRY(w.lmers.ensure(lmer_bytes(lay) * lmer_total, c->held));
     PMS_TRY(w.items.ensure(sizeof(Item) * std::max<uint64_t>(item_cap, 1), c->held));
-    PMS_TRY(w.lists.ensure(4ull * nwarps * levels * list_cap, c->held));
     const uint64_t fstride = (search_frontier_bytes(lay, lmax) + 255) & ~uint64_t(255);
-    PMS_TRY(w.fscr.ensure(fstride * nwarps, c->held));
+    // per-warp scratch of a search launch with threshold tt
+    auto scratch = [&](int tt, const LaunchCfg &cf) {
+        const uint64_t nw = (uint64_t)cf.blocks * cf.warps_per_block;
+        int rc = w.lists.ensure(4ull * nw * search_levels(tt) * list_cap, c->held);
+        if (rc == PMS_OK)
+            rc = w.fscr.ensure(fstride * nw, c->held);
+        return rc;
+    };
+    PMS_TRY(scratch(t, cfg));
     PMS_TRY(w.keys.ensure(16 * key_cap, c->held));
     PMS_TRY(w.counters.ensure(sizeof(Counters), c->held));
     PMS_TRY(w.first.ensure(8 * (size_t)ninst, c->held));
@@ -412,16 +437,48 @@ int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
                         w.items.as<Item>(), &dc->item_count, item_cap, &dc->status, &dc->stats,
                         s));
     uint64_t launches = (lmer_total ? 1 : 0) + (x_total ? 1 : 0);
-    Counters hc{};
-    for (int attempt = 0;; attempt++) {
-        launches++;
-        PMS_CU(cudaEventRecord(w.ev[1], s));
+    auto search = [&](int tt, const LaunchCfg &cf, int stride) {
         SearchArgs sa{w.inst.as<InstDesc>(), w.lmers.p, w.items.as<Item>(), &dc->item_count,
                       item_cap, &dc->item_next, w.lists.as<uint32_t>(), list_cap,
                       w.keys.as<uint64_t>(), &dc->key_count, key_cap, &dc->status,
-                      &dc->stats, key_bits, multi, cfg, w.fscr.as<unsigned char>(), fstride,
-                      lmax};
-        PMS_CU(launch_search(lay, t, sa, s));
+                      &dc->stats, key_bits, multi, cf, w.fscr.as<unsigned char>(), fstride,
+                      lmax, stride};
+        return launch_search(lay, tt, sa, s);
+    };
+    Counters hc{};
+    if (tune) {
+        // Section 2.2: the threshold is found empirically on a small subset of the tuples.
+        unsigned long long nitems = 0;
+        PMS_CU(copy(&nitems, &dc->item_count, sizeof nitems, cudaMemcpyDeviceToHost, s));
+        PMS_CU(cudaStreamSynchronize(s));
+        const int stride = (int)std::max<unsigned long long>(1, nitems / 1024);
+        float best_ms = INFINITY;
+        tune->ms.clear();
+        for (int tt : tune->cand) {
+            LaunchCfg cf{};
+            PMS_TRY(shape(tt, cf));
+            PMS_TRY(scratch(tt, cf));
+            unsigned long long zero[2] = {0, 0};
+            PMS_CU(cudaMemcpyAsync(&dc->item_next, zero, 16, cudaMemcpyHostToDevice, s));
+            PMS_CU(cudaMemsetAsync(&dc->status, 0, sizeof(int), s));
+            PMS_CU(cudaEventRecord(w.ev[1], s));
+            PMS_CU(search(tt, cf, stride));
+            PMS_CU(cudaEventRecord(w.ev[2], s));
+            PMS_CU(cudaStreamSynchronize(s));
+            float ms = 0;
+            cudaEventElapsedTime(&ms, w.ev[1], w.ev[2]);
+            tune->ms.push_back(ms);
+            if (ms < best_ms) {
+                best_ms = ms;
+                tune->best = tt;
+            }
+        }
+        return PMS_OK;
+    }
+    for (int attempt = 0;; attempt++) {
+        launches++;
+        PMS_CU(cudaEventRecord(w.ev[1], s));
+        PMS_CU(search(t, cfg, 1));
         PMS_CU(cudaEventRecord(w.ev[2], s));
         PMS_CU(copy(&hc, dc, sizeof hc, cudaMemcpyDeviceToHost, s));
         PMS_CU(cudaStreamSynchronize(s));
@@ -551,10 +608,49 @@ int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
     return PMS_OK;
 }
 
+// Autotuner: the first time an instance class (tune_key) is seen, time
+// the search on a sample of its items for the thresholds around the Appendix D model
+// and cache the fastest.  The motif set does not depend on the threshold.
+void autotune(pms_ctx *c, Workspace &w, const Prep &p)
+{
+    const auto key = tune_key(p);
+    {
+        std::lock_guard<std::mutex> g(c->tune_mu);
+        if (c->tune.count(key))
+            return;
+    }
+    const int model = model_threshold(p.n, p.m, p.l, p.d, p.k);
+    const int hi = std::min(p.n, kTMax);
+    Tune tu;
+    for (int t = std::max(2, std::min(model - 1, 3)); t <= std::min(hi, std::max(model + 1, 5));
+         t++)
+        if (!(p.d > 41 && t < 5))
+            tu.cand.push_back(t);
+    int chosen = model;
+    if (tu.cand.size() > 1 && p.n >= 3) {
+        std::vector<Prep> one{p};
+        one[0].t = tu.cand[0];
+        one[0].xb = 0;
+        one[0].xe = p.L;
+        BatchOut bo;
+        std::vector<pms_result> dummy(1);
+        bo.host = &dummy;
+        bo.rc.assign(1, PMS_OK);
+        std::vector<int> idx{0};
+        if (run_group(c, w, one, bo, idx, nullptr, &tu) == PMS_OK && tu.best)
+            chosen = tu.best;
+    }
+    std::lock_guard<std::mutex> g(c->tune_mu);
+    c->tune[key] = chosen;
+}
+
 // Split a batch into groups that can share one launch sequence (same plane layout, key
 // room for the instance id) and run each.
 int run_batch(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo, pms_stats *agg)
 {
+    if (!c->opts.threshold)
+        for (auto &p : ins)
+            autotune(c, w, p);
     std::map<int, std::vector<int>> groups;
     for (int i = 0; i < (int)ins.size(); i++) {
         ins[i].t = threshold_for(c, ins[i]);
@@ -834,13 +930,15 @@ int pms_solve_device(pms_ctx *c, const char *d_seqs, int n, int m, const char *a
     if (rc != PMS_OK)
         return rc;
     ins[0].on_device = true;
-    ins[0].t = threshold_for(c, ins[0]);
     std::lock_guard<std::mutex> g(c->solve_mu);
     if (cudaSetDevice(c->device) != cudaSuccess)
         return PMS_E_CUDA;
     cudaStream_t saved = c->main.stream;
     if (stream)
         c->main.stream = static_cast<cudaStream_t>(stream);
+    if (!c->opts.threshold)
+        autotune(c, c->main, ins[0]);
+    ins[0].t = threshold_for(c, ins[0]);
     BatchOut bo;
     bo.dev_motifs = d_motifs;
     bo.dev_cap = cap;

@@ -130,6 +130,7 @@ struct SearchArgs {
     unsigned char *fscr;      // scratch: frontier-enumeration tables and levels per warp
     uint64_t fscr_stride;     // bytes per warp (search_frontier_bytes(lay, lmax))
     int lmax;                 // longest l in the batch
+    int item_stride;          // search items 0, s, 2s, ... only (autotuner samples); 1 = all
 };
 
 // Lists each search warp keeps for threshold t (levels 2..t-1, at least one).

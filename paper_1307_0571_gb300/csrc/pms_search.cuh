@@ -31,6 +31,12 @@ namespace search {
 
 using namespace dev;
 
+#ifndef PMS_SEARCH_MIN_BLOCKS
+#define PMS_SEARCH_MIN_BLOCKS 5
+#endif
+// Resident 4-warp blocks per SM the register allocation must allow.
+constexpr int kSearchMinBlocks = PMS_SEARCH_MIN_BLOCKS;
+
 template <int NB, typename W, int T>
 struct WarpSm {
     Lm<NB, W> stk[T];
@@ -537,9 +543,10 @@ __device__ __forceinline__ void rot_selectors(int tk, uint32_t &r1, uint32_t &r2
 }
 
 // Limits of one tuple for prefix length q = l down to 0, and the letters of its l-mers
-// at each position: tbl[q] = {letters at q, pair limits (i,i+1), pair limits (i,i+2),
-// triple limits (i,i+1,i+2)}.  Returns false when the tuple itself fails the pair or
-// triple condition (no common neighbour, Theorem 1).
+// at each position: tbl[q] = {letters at position q-1, pair limits (i,i+1), pair limits
+// (i,i+2), triple limits (i,i+1,i+2)} for prefix length q, so testing a child at position
+// p reads the single entry tbl[p+1].  Returns false when the tuple itself fails the pair
+// or triple condition (no common neighbour, Theorem 1).
 template <int NB, typename W, int T>
 __device__ bool tuple_table(const Lm<NB, W> (&st)[T], int tk, int l, int d, uint4 *tbl)
 {
@@ -600,8 +607,8 @@ __device__ bool tuple_table(const Lm<NB, W> (&st)[T], int tk, int l, int d, uint
                     ok = ok && v >= 0;
                     lim3 = (lim3 & ~(0xFFu << sh)) | ((uint32_t)(v < 0 ? 0 : v) << sh);
                 }
-                if (q < l)
-                    codes |= (uint32_t)get_letter(st[i], q) << sh;
+                if (q > 0)
+                    codes |= (uint32_t)get_letter(st[i], q - 1) << sh;
             }
         }
         tbl[q] = make_uint4(codes, lim1, lim2, lim3);
@@ -675,12 +682,16 @@ __device__ void enumerate_frontier(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &
         int deepest = __popc(bal) ? 0 : -1;
         __syncwarp();
         while (deepest >= 0) {
+            {
+                // deepest non-empty level: the highest lane whose count is non-zero
+                const unsigned hi = __ballot_sync(kFull, cnt_hi > 0);
+                const unsigned lo = __ballot_sync(kFull, cnt_lo > 0);
+                deepest = hi ? 63 - __clz(hi) : lo ? 31 - __clz(lo) : -1;
+                if (deepest < 0)
+                    break;
+            }
             const int p = deepest;
             const int have = __shfl_sync(kFull, p < 32 ? cnt_lo : cnt_hi, p & 31);
-            if (have == 0) {
-                deepest--;
-                continue;
-            }
             const int c = have < chunk ? have : chunk;
             const int first = have - c;
             if (lane == (p & 31)) {
@@ -692,11 +703,9 @@ __device__ void enumerate_frontier(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &
             bool ok = false;
             FNode<NB, W> child;
             if (my_node < c) {
-                const FNode<NB, W> nd = front[(size_t)p * kFrontCap + first + my_node];
-                const uint4 *tb = tbl_all + (size_t)nd.b * (l + 1);
-                const uint32_t codes = tb[p].x;
-                const uint4 lim = tb[p + 1];
-                const uint32_t x = codes ^ alpha_rep;
+                const FNode<NB, W> nd = front[(unsigned)p * kFrontCap + first + my_node];
+                const uint4 lim = tbl_all[nd.b * (unsigned)(l + 1) + (unsigned)(p + 1)];
+                const uint32_t x = lim.x ^ alpha_rep;
                 const uint32_t inc =
                     (((((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x) & 0x80808080u) >> 7) & used;
                 const uint32_t e = nd.e + inc;
@@ -731,14 +740,13 @@ __device__ void enumerate_frontier(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &
             } else if (okb) {
                 // the level below is empty: its nodes start at 0
                 if (ok)
-                    front[(size_t)(p + 1) * kFrontCap + __popc(okb & lanemask_lt())] = child;
+                    front[(unsigned)(p + 1) * kFrontCap + __popc(okb & lanemask_lt())] = child;
                 if (lane == ((p + 1) & 31)) {
                     if (p + 1 < 32)
                         cnt_lo = __popc(okb);
                     else
                         cnt_hi = __popc(okb);
                 }
-                deepest = p + 1;
                 __syncwarp();
             }
         }
@@ -846,12 +854,13 @@ __device__ void run_item(WarpSm<NB, W, T> &S, SearchCtx<NB, W> &C, const Item &i
 }
 
 template <int NB, typename W, int T>
-__global__ void __launch_bounds__(128) search_kernel(
+__global__ void __launch_bounds__(128, kSearchMinBlocks) search_kernel(
     const InstDesc *__restrict__ inst, const Lm<NB, W> *__restrict__ lmers,
     const Item *__restrict__ items, const unsigned long long *item_count, uint64_t item_cap,
     unsigned long long *item_next, uint32_t *lists, uint64_t list_cap, uint64_t *keys,
     unsigned long long *key_count, uint64_t key_cap, int *status, DevStats *stats,
-    int key_shift, int multi, unsigned char *fscr, uint64_t fscr_stride, int lmax)
+    int key_shift, int multi, unsigned char *fscr, uint64_t fscr_stride, int lmax,
+    int item_stride)
 {
     extern __shared__ unsigned char smem_raw[];
     WarpSm<NB, W, T> &S = reinterpret_cast<WarpSm<NB, W, T> *>(smem_raw)[threadIdx.x >> 5];
@@ -871,7 +880,8 @@ __global__ void __launch_bounds__(128) search_kernel(
     C.multi = multi;
     WarpCounters wc;
     unsigned long long done = 0;
-    const unsigned long long nitems = *item_count < item_cap ? *item_count : item_cap;
+    const unsigned long long nall = *item_count < item_cap ? *item_count : item_cap;
+    const unsigned long long nitems = (nall + item_stride - 1) / item_stride;
     for (;;) {
         unsigned long long it = 0;
         if (lane == 0)
@@ -879,7 +889,7 @@ __global__ void __launch_bounds__(128) search_kernel(
         it = __shfl_sync(kFull, it, 0);
         if (it >= nitems)
             break;
-        const Item item = items[it];
+        const Item item = items[it * item_stride];
         C.I = inst + item.inst;
         C.inst = (int)item.inst;
         C.lm = lmers + C.I->lmer_off;
@@ -918,7 +928,7 @@ cudaError_t launch(const SearchArgs &a, cudaStream_t s)
     search_kernel<NB, W, T><<<a.cfg.blocks, a.cfg.warps_per_block * 32, smem, s>>>(
         a.inst, static_cast<const Lm<NB, W> *>(a.lmers), a.items, a.item_count, a.item_cap,
         a.item_next, a.lists, a.list_cap, a.keys, a.key_count, a.key_cap, a.status, a.stats,
-        a.key_shift, a.multi, a.fscr, a.fscr_stride, a.lmax);
+        a.key_shift, a.multi, a.fscr, a.fscr_stride, a.lmax, a.item_stride > 0 ? a.item_stride : 1);
     return cudaGetLastError();
 }
 
