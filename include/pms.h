@@ -138,6 +138,38 @@ int pms_solve_device(pms_ctx *ctx, const char *d_seqs, int n, int m, const char 
                      int l, int d, char *d_motifs, uint64_t cap, uint64_t *count,
                      void *stream, pms_stats *stats);
 
+/*
+ * The device-resident solve of pms_solve_device for callers that must not allocate device
+ * memory once running: a service that reserves its device memory in its own pool at
+ * start-up, so a later cudaMalloc would fail or break its budget, or a real-time pipeline
+ * in which cudaMalloc/cudaFree would stall the device and fragment memory.  It needs no
+ * context and creates no stream, event or buffer.  (The paper has no counterpart; this is
+ * a deployment interface.)
+ *
+ * All working memory is one fixed 64 MiB array inside the library's device image, which
+ * every device that loads the library holds until the process exits.  The caller passes
+ * the strings (d_seqs, device, n*m bytes) and the output buffer (d_motifs, device, room
+ * for cap*l bytes); *count (host) receives the number of motifs.  Arguments as in
+ * pms_solve_device, plus threshold (2..8, or 0 for the Appendix D cost model; no
+ * autotuning, which would allocate).  Runs on the current device and on `stream` (NULL =
+ * the default stream) and returns after the work on it has finished.
+ *
+ * Limits: the request must fit the fixed array: the l-mer table, one item per compatible
+ * (x, u) pair of up to (m-l+1)^2, at most 262144 raw motif finds, and per-warp search
+ * lists of (n-1)*(m-l+1) entries for at least 32 warps.  A request that does not fit
+ * returns PMS_E_NOMEM (nothing runs); more raw finds than fit returns PMS_E_OVERFLOW.
+ * With the default threshold, DNA instances up to n=20, m=1000 fit.
+ *
+ * The first call on each device looks up the array's device address; make that first call
+ * before any stream capture.  Every call reuses the same array (each call clears what it
+ * needs), so calls must not overlap on the GPU: calls from several host threads are
+ * serialised inside the library, but two processes or overlapping streams sharing a
+ * device must not call it at the same time.
+ */
+int pms_solve_device_noalloc(const char *d_seqs, int n, int m, const char *alphabet, int l,
+                             int d, int threshold, char *d_motifs, uint64_t cap,
+                             uint64_t *count, void *stream);
+
 /* Serving: queue an instance (inputs are copied before return) and get a ticket. */
 int pms_submit(pms_ctx *ctx, const pms_instance *inst, uint64_t *ticket);
 

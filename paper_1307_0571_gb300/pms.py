@@ -32,7 +32,7 @@ PMS_E_NOTFOUND = -8
 
 EXPORTS = ["pms_create", "pms_destroy", "pms_solve", "pms_solve_batch", "pms_solve_device",
            "pms_submit", "pms_poll", "pms_result_free", "pms_strerror",
-           "pms_autotune_entries", "pms_autotune_reset"]
+           "pms_autotune_entries", "pms_autotune_reset", "pms_solve_device_noalloc"]
 
 
 class pms_opts(ctypes.Structure):
@@ -107,8 +107,28 @@ def load() -> ctypes.CDLL:
         lib.pms_autotune_entries.argtypes = [ctypes.c_void_p]
         lib.pms_autotune_reset.argtypes = [ctypes.c_void_p]
         lib.pms_autotune_reset.restype = None
+        lib.pms_solve_device_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                                 ctypes.c_char_p, ctypes.c_int, ctypes.c_int,
+                                                 ctypes.c_int, ctypes.c_void_p,
+                                                 ctypes.c_uint64, P(ctypes.c_uint64),
+                                                 ctypes.c_void_p]
         _lib = lib
         return lib
+
+
+def solve_device_noalloc(d_seqs: int, n: int, m: int, alphabet: str, l: int, d: int,
+                         d_motifs: int, cap: int, stream: int = 0, threshold: int = 0) -> int:
+    """pms_solve_device_noalloc: the device-resident solve using only the library's fixed
+    scratch array (for callers that must not allocate device memory while running).
+    Returns the motif count; the motifs are in d_motifs."""
+    lib = load()
+    cnt = ctypes.c_uint64(0)
+    rc = lib.pms_solve_device_noalloc(ctypes.c_void_p(d_seqs), n, m, alphabet.encode("ascii"),
+                                      l, d, threshold, ctypes.c_void_p(d_motifs), cap,
+                                      ctypes.byref(cnt), ctypes.c_void_p(stream))
+    if rc != PMS_OK:
+        raise PMSError(rc, "pms_solve_device_noalloc")
+    return cnt.value
 
 
 def strerror(code: int) -> str:
