@@ -95,6 +95,9 @@ typedef struct pms_stats {
     uint64_t search_ops;      /* algorithmic integer ops of the search kernel (unit costs in
                                  the library's documentation of the roofline) */
     uint64_t launches;        /* kernels launched by the solve */
+    uint64_t busy_max;        /* search kernel: largest per-warp busy time (SM cycles) */
+    uint64_t busy_mean;       /* search kernel: mean per-warp busy time (SM cycles) */
+    uint64_t item_max;        /* search kernel: most cycles a single (x, u) item took */
     uint64_t h2d_bytes;       /* bytes copied host -> device by the solve */
     uint64_t d2h_bytes;       /* bytes copied device -> host by the solve */
     double kernel_ms;         /* device time of the whole solve (CUDA events) */

@@ -6,6 +6,7 @@
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <deque>
@@ -79,7 +80,15 @@ struct Counters {           // one device block of small counters
     int status;
     int pad;
     DevStats stats;
+    unsigned long long donate_count[2];
 };
+
+// Items handed on per search pass (ping-pong buffers), and the time an item runs before
+// it hands on the rest of its range (cycles; ~2 ms at 2 GHz).  Splitting happens only
+// once a pass has handed out all its items, so it trims the tail that the heaviest items
+// (100x the median) would otherwise set, without repeating work earlier in the pass.
+constexpr uint64_t kDonateCap = 1u << 20;
+constexpr long long kItemBudget = 4000000;
 
 // Everything one pipeline run needs on the device; a context owns one for blocking calls
 // and one per serving slot, so slots run concurrently on their own streams.
@@ -87,11 +96,12 @@ struct Workspace {
     cudaStream_t stream = nullptr;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     DBuf seqs, maps, inst, alpha, lmers, items, lists, fscr, keys, keys_alt, hist, flags,
-        out_chars, byte_off, first, last, counters;
+        out_chars, byte_off, first, last, counters, don0, don1, trace;
     std::vector<DBuf *> all()
     {
         return {&seqs, &maps, &inst, &alpha, &lmers, &items, &lists, &fscr, &keys, &keys_alt,
-                &hist, &flags, &out_chars, &byte_off, &first, &last, &counters};
+                &hist, &flags, &out_chars, &byte_off, &first, &last, &counters, &don0, &don1,
+                &trace};
     }
 };
 
@@ -383,8 +393,18 @@ int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
     PMS_TRY(shape(t, cfg));
     (void)levels;
 
-    // buffers
-    uint64_t key_cap = std::max<uint64_t>(1 << 16, w.keys.cap / 16);
+    // buffers; the raw motif list is sized from the expected number of motifs of random
+    // strings (Appendix C: |S|^l q^n, q = 1 - (1 - N_d/|S|^l)^(m-l+1)) times the number of
+    // finds per motif seen in practice (2.5-5), so reruns after an overflow are rare
+    double expect = 0;
+    for (const Prep &p : ins) {
+        const double nd = nbhd(p.l, p.d, p.k), total = std::pow((double)p.k, p.l);
+        const double q = 1.0 - std::pow(1.0 - std::min(1.0, nd / total), (double)p.L);
+        expect += std::min(total, total * std::pow(q, p.n)) + 1.0;
+    }
+    const double want_keys = std::min(6.0 * expect + 65536.0,
+                                      (double)std::max<uint64_t>(c->opts.max_motifs, 1) * 8.0);
+    uint64_t key_cap = std::max<uint64_t>((uint64_t)want_keys, w.keys.cap / 16);
     PMS_TRY(w.seqs.ensure(seq_total, c->held));
     PMS_TRY(w.maps.ensure(256 * (size_t)ninst, c->held));
     PMS_TRY(w.alpha.ensure(32 * (size_t)ninst, c->held));
@@ -403,6 +423,8 @@ int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
     PMS_TRY(scratch(t, cfg));
     PMS_TRY(w.keys.ensure(16 * key_cap, c->held));
     PMS_TRY(w.counters.ensure(sizeof(Counters), c->held));
+    PMS_TRY(w.don0.ensure(sizeof(Item) * kDonateCap, c->held));
+    PMS_TRY(w.don1.ensure(sizeof(Item) * kDonateCap, c->held));
     PMS_TRY(w.first.ensure(8 * (size_t)ninst, c->held));
     PMS_TRY(w.last.ensure(8 * (size_t)ninst, c->held));
     PMS_TRY(w.byte_off.ensure(8 * (size_t)ninst, c->held));
@@ -437,13 +459,43 @@ int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
                         w.items.as<Item>(), &dc->item_count, item_cap, &dc->status, &dc->stats,
                         s));
     uint64_t launches = (lmer_total ? 1 : 0) + (x_total ? 1 : 0);
-    auto search = [&](int tt, const LaunchCfg &cf, int stride) {
-        SearchArgs sa{w.inst.as<InstDesc>(), w.lmers.p, w.items.as<Item>(), &dc->item_count,
-                      item_cap, &dc->item_next, w.lists.as<uint32_t>(), list_cap,
-                      w.keys.as<uint64_t>(), &dc->key_count, key_cap, &dc->status,
-                      &dc->stats, key_bits, multi, cf, w.fscr.as<unsigned char>(), fstride,
-                      lmax, stride};
-        return launch_search(lay, tt, sa, s);
+    // Optional per-item profile (env PMS_ITEM_TRACE = output file, binary ItemTrace records
+    // of the first pass): a profiling aid, off by default.
+    const char *trace_path = std::getenv("PMS_ITEM_TRACE");
+    ItemTrace *trace = nullptr;
+    if (trace_path && *trace_path && !tune) {
+        PMS_TRY(w.trace.ensure(sizeof(ItemTrace) * std::max<uint64_t>(item_cap, 1), c->held));
+        trace = w.trace.as<ItemTrace>();
+    }
+    // The search: pass 0 over the items, then passes over the items handed on by
+    // subproblems that ran past their budget, until none are.
+    auto search = [&](int tt, const LaunchCfg &cf, int stride) -> int {
+        Item *don[2] = {w.don0.as<Item>(), w.don1.as<Item>()};
+        for (int pass = 0;; pass++) {
+            const bool first_pass = pass == 0;
+            const int out = pass & 1;
+            unsigned long long zero = 0;
+            PMS_CU(cudaMemcpyAsync(&dc->item_next, &zero, 8, cudaMemcpyHostToDevice, s));
+            PMS_CU(cudaMemcpyAsync(&dc->donate_count[out], &zero, 8, cudaMemcpyHostToDevice,
+                                   s));
+            SearchArgs sa{w.inst.as<InstDesc>(), w.lmers.p,
+                          first_pass ? w.items.as<Item>() : don[out ^ 1],
+                          first_pass ? &dc->item_count : &dc->donate_count[out ^ 1],
+                          first_pass ? item_cap : kDonateCap, &dc->item_next,
+                          w.lists.as<uint32_t>(), list_cap, w.keys.as<uint64_t>(),
+                          &dc->key_count, key_cap, &dc->status, &dc->stats, key_bits, multi,
+                          cf, w.fscr.as<unsigned char>(), fstride, lmax,
+                          first_pass ? stride : 1, don[out], &dc->donate_count[out],
+                          kDonateCap, kItemBudget, first_pass ? trace : nullptr};
+            PMS_CU(launch_search(lay, tt, sa, s));
+            launches++;
+            unsigned long long handed = 0;
+            PMS_CU(cudaMemcpyAsync(&handed, &dc->donate_count[out], 8, cudaMemcpyDeviceToHost,
+                                   s));
+            PMS_CU(cudaStreamSynchronize(s));
+            if (handed == 0)
+                return PMS_OK;
+        }
     };
     Counters hc{};
     if (tune) {
@@ -462,7 +514,7 @@ int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
             PMS_CU(cudaMemcpyAsync(&dc->item_next, zero, 16, cudaMemcpyHostToDevice, s));
             PMS_CU(cudaMemsetAsync(&dc->status, 0, sizeof(int), s));
             PMS_CU(cudaEventRecord(w.ev[1], s));
-            PMS_CU(search(tt, cf, stride));
+            PMS_TRY(search(tt, cf, stride));
             PMS_CU(cudaEventRecord(w.ev[2], s));
             PMS_CU(cudaStreamSynchronize(s));
             float ms = 0;
@@ -476,9 +528,8 @@ int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
         return PMS_OK;
     }
     for (int attempt = 0;; attempt++) {
-        launches++;
         PMS_CU(cudaEventRecord(w.ev[1], s));
-        PMS_CU(search(t, cfg, 1));
+        PMS_TRY(search(t, cfg, 1));
         PMS_CU(cudaEventRecord(w.ev[2], s));
         PMS_CU(copy(&hc, dc, sizeof hc, cudaMemcpyDeviceToHost, s));
         PMS_CU(cudaStreamSynchronize(s));
@@ -501,6 +552,16 @@ int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
         PMS_CU(copy(&dc->item_next, zero, 16, cudaMemcpyHostToDevice, s));
         PMS_CU(cudaMemsetAsync(&dc->status, 0, sizeof(int), s));
         PMS_CU(cudaMemsetAsync(&dc->stats, 0, sizeof(DevStats), s));
+    }
+
+    if (trace) {
+        const uint64_t n = std::min<uint64_t>(hc.item_count, item_cap);
+        std::vector<ItemTrace> recs(n);
+        PMS_CU(cudaMemcpy(recs.data(), trace, sizeof(ItemTrace) * n, cudaMemcpyDeviceToHost));
+        if (FILE *f = std::fopen(trace_path, "wb")) {
+            std::fwrite(recs.data(), sizeof(ItemTrace), n, f);
+            std::fclose(f);
+        }
     }
 
     // collect: sort, unique, per-instance ranges
@@ -567,6 +628,9 @@ int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
     st.cyc_verify = hc.stats.cyc_verify;
     st.search_ops = hc.stats.search_ops;
     st.launches = launches;
+    st.busy_max = hc.stats.busy_max;
+    st.busy_mean = hc.stats.warps ? hc.stats.busy_sum / hc.stats.warps : 0;
+    st.item_max = hc.stats.item_max;
     st.h2d_bytes = h2d;
     st.d2h_bytes = d2h;
     st.kernel_ms = total_ms;
@@ -687,6 +751,9 @@ int run_batch(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo, pm
             total.cyc_verify += st.cyc_verify;
             total.search_ops += st.search_ops;
             total.launches += st.launches;
+            total.busy_max = std::max(total.busy_max, st.busy_max);
+            total.busy_mean = std::max(total.busy_mean, st.busy_mean);
+            total.item_max = std::max(total.item_max, st.item_max);
             total.h2d_bytes += st.h2d_bytes;
             total.d2h_bytes += st.d2h_bytes;
             total.kernel_ms += st.kernel_ms;

@@ -34,13 +34,29 @@ struct InstDesc {
 
 // One (x, u) subproblem: x = S_1[x..], u = S_b[u..] with Hd(x,u) <= 2d and b the
 // smallest row of the 2d filter (Section 2.1 "Sort rows by size").  b = 0xFFFF marks a
-// single-string instance (no u).
+// single-string instance (no u).  [lo, hi) restricts the subproblem to those positions
+// of the level-2 branch row (the stack's third l-mer; for threshold 3 the tuples of the
+// enumeration): a subproblem that runs past its time budget hands the rest of its range
+// to other warps as items with narrower ranges.  hi = 0xFFFF means the whole row.
+//   With threshold 4 an item can also stand for one level-2 position p2 = lo (hi = lo+1)
+// and the tuples [lo3, hi3) of the branch row below it; hi3 = 0xFFFF means "not so".
 struct Item {
     uint32_t inst;
     uint16_t x;
     uint16_t u;
     uint16_t b;
+    uint16_t lo;
+    uint16_t hi;
+    uint16_t lo3;
+    uint16_t hi3;
     uint16_t pad;
+};
+constexpr uint16_t kAllRange = 0xFFFF;
+
+// Per-item profile record (written only when tracing is on; see PMS_ITEM_TRACE).
+struct ItemTrace {
+    Item item;
+    unsigned long long cycles, nodes, leaves, tuples;
 };
 
 // Counters the kernels accumulate (one struct in device memory per solve).
@@ -55,6 +71,10 @@ struct DevStats {
     unsigned long long cyc_enum;
     unsigned long long cyc_verify;
     unsigned long long search_ops;   // algorithmic integer ops of the search kernel
+    unsigned long long busy_max;     // largest per-warp busy time (cycles)
+    unsigned long long busy_sum;     // per-warp busy time summed over warps
+    unsigned long long warps;        // warps of the search launch
+    unsigned long long item_max;     // most cycles one item took
 };
 
 // Algorithmic integer-op counts per unit of work, for NB planes of 32-bit words (64-bit
@@ -64,8 +84,10 @@ struct DevStats {
 //   Theorem 1 triple, given D(s,top)  NB + 6  (diff, or, popc, and3, popc, add, compare)
 //   level-2 test (x, u, v)            2 NB + 10
 //   filter test at stack size k       NB + 2 + k (NB + 6)
-//   frontier child (packed budgets)   25 + 2 NB (letter mismatch bytes, 3 byte permutes,
-//                                     3 adds, 4 byte-wise compares, set the letter)
+//   Lemma 1 for four l-mers (filter)  14      (3 masks of 2-3 logic ops, 3 popc, adds)
+//   frontier child (packed budgets)   29 + 2 NB (letter mismatch bytes, 3 byte permutes,
+//                                     3 adds, 4 byte-wise compares, the budget sum and its
+//                                     compare, set the letter)
 //   per-lane walk node, tuple of tk   tk (NB + 3) + 5 C(tk,2) + 9 C(tk,3)
 __host__ __device__ inline unsigned long long op_hd(int nb) { return nb + 2; }
 __host__ __device__ inline unsigned long long op_level2(int nb) { return 2 * nb + 10; }
@@ -73,7 +95,8 @@ __host__ __device__ inline unsigned long long op_filter(int nb, int k)
 {
     return nb + 2 + (unsigned long long)k * (nb + 6);
 }
-__host__ __device__ inline unsigned long long op_child(int nb) { return 25 + 2 * nb; }
+__host__ __device__ inline unsigned long long op_lemma4() { return 14; }
+__host__ __device__ inline unsigned long long op_child(int nb) { return 29 + 2 * nb; }
 __host__ __device__ inline unsigned long long op_walk(int nb, int tk)
 {
     return (unsigned long long)tk * (nb + 3) + 5ull * tk * (tk - 1) / 2 +
@@ -131,6 +154,11 @@ struct SearchArgs {
     uint64_t fscr_stride;     // bytes per warp (search_frontier_bytes(lay, lmax))
     int lmax;                 // longest l in the batch
     int item_stride;          // search items 0, s, 2s, ... only (autotuner samples); 1 = all
+    Item *donate;             // items handed on by subproblems past their budget
+    unsigned long long *donate_count;
+    uint64_t donate_cap;
+    long long budget;         // cycles an item runs before it hands on the rest of its range
+    ItemTrace *trace;         // per-item records of the first pass, or null
 };
 
 // Lists each search warp keeps for threshold t (levels 2..t-1, at least one).

@@ -233,7 +233,8 @@ int solve_noalloc(const char *d_seqs, int n, int m, const char *alphabet, int l,
                   reinterpret_cast<uint32_t *>(base + o_lists), list_cap,
                   reinterpret_cast<uint64_t *>(base + o_keys), &dc->key_count, kNoAllocRawKeys,
                   &dc->status, &dc->stats, l * kbits, 0,
-                  LaunchCfg{wpb, (int)blocks}, base + o_fscr, fstride, l, 1};
+                  LaunchCfg{wpb, (int)blocks}, base + o_fscr, fstride, l, 1, nullptr, nullptr,
+                  0, 0, nullptr};
     NA_CU(launch_search(lay, t, sa, s));
     NaCounters hc;
     NA_CU(cudaMemcpyAsync(&hc, dc, sizeof hc, cudaMemcpyDeviceToHost, s));

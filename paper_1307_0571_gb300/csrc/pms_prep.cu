@@ -66,7 +66,7 @@ __global__ void items_kernel(const InstDesc *__restrict__ inst, int ninst, uint6
             if (lane == 0) {
                 unsigned long long pos = atomicAdd(item_count, 1ull);
                 if (pos < item_cap)
-                    items[pos] = Item{(uint32_t)ii, (uint16_t)x, 0, 0xFFFF, 0};
+                    items[pos] = Item{(uint32_t)ii, (uint16_t)x, 0, 0xFFFF, 0, kAllRange, 0, kAllRange, 0};
                 else
                     atomicOr(status, kErrItemsOverflow);
             }
@@ -105,7 +105,8 @@ __global__ void items_kernel(const InstDesc *__restrict__ inst, int ninst, uint6
             if (ok) {
                 unsigned long long pos = base + __popc(bal & lanemask_lt());
                 if (pos < item_cap)
-                    items[pos] = Item{(uint32_t)ii, (uint16_t)x, (uint16_t)j, (uint16_t)brow, 0};
+                    items[pos] = Item{(uint32_t)ii, (uint16_t)x, (uint16_t)j, (uint16_t)brow, 0,
+                                      kAllRange, 0, kAllRange, 0};
                 else
                     atomicOr(status, kErrItemsOverflow);
             }

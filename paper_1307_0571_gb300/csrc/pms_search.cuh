@@ -72,7 +72,67 @@ struct SearchCtx {
     int *status;
     int key_shift;
     int multi;
+    Item item;                // the item being searched
+    long long t0;             // its start (clock64, lane 0's)
+    Item *donate;
+    unsigned long long *donate_count;
+    uint64_t donate_cap;
+    long long budget;
+    const unsigned long long *item_next;   // the pass's item counter
+    unsigned long long nitems;             // items of this pass
 };
+
+// Work splitting: an item that has run longer than the budget hands the positions
+// [pos, end) of its range to other warps as up to 64 items with narrower ranges (the
+// receiving warp rebuilds the same lists, which are deterministic).  With p2 < 0 the
+// range is the item's level-2 range (for threshold 3, its tuples); with p2 >= 0 it is the
+// tuples of the level-3 branch row under level-2 position p2 (threshold 4).  Returns true
+// when the rest was handed on (the caller stops), false to keep going.
+template <int NB, typename W>
+__device__ bool maybe_donate(const SearchCtx<NB, W> &C, int pos, int end, int lane,
+                             int p2 = -1)
+{
+    if (!C.donate || end - pos < 2)
+        return false;
+    long long now = clock64();
+    now = __shfl_sync(kFull, now, 0);
+    if (now - C.t0 < C.budget)
+        return false;
+    // only once every item of the pass has been taken: until then idle warps have other
+    // work, and splitting would only repeat list building
+    unsigned long long taken = 0;
+    if (lane == 0)
+        taken = *(volatile const unsigned long long *)C.item_next;
+    if (__shfl_sync(kFull, taken, 0) < C.nitems)
+        return false;
+    const int R = end - pos;
+    const int chunk = (R + 63) / 64;
+    const int nsub = (R + chunk - 1) / chunk;
+    unsigned long long base = 0;
+    if (lane == 0)
+        base = atomicAdd(C.donate_count, (unsigned long long)nsub);
+    base = __shfl_sync(kFull, base, 0);
+    if (base + nsub > C.donate_cap)
+        return false;   // no room: keep searching here (the count only sizes the next pass)
+    for (int i = lane; i < nsub; i += 32) {
+        Item sub = C.item;
+        const uint16_t a = (uint16_t)(pos + i * chunk);
+        const uint16_t b = (uint16_t)(pos + i * chunk + chunk < end ? pos + i * chunk + chunk : end);
+        if (p2 < 0) {
+            sub.lo = a;
+            sub.hi = b;
+            sub.lo3 = 0;
+            sub.hi3 = kAllRange;
+        } else {
+            sub.lo = (uint16_t)p2;
+            sub.hi = (uint16_t)(p2 + 1);
+            sub.lo3 = a;
+            sub.hi3 = b;
+        }
+        C.donate[base + i] = sub;
+    }
+    return true;
+}
 
 // Row with the fewest survivors at level k (Section 2.1 "Sort rows by size": the next
 // stack element comes from the smallest row).  Ties go to the lower string index.
@@ -163,8 +223,9 @@ __device__ bool build_level2(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &C, int
 // Push stk[k] (stack size becomes k+1) and filter the rows of level k other than the
 // branch row into level k+1: v survives when Hd(top,v) <= 2d and, for every earlier stack
 // l-mer s, Cd(s, top, v) <= 3d (Theorem 1 with budgets d,d,d; the pair conditions with
-// earlier l-mers hold from earlier levels).  Returns false as soon as a row empties
-// (Section 2: "If any row becomes empty ... try a different l-mer").
+// earlier l-mers hold from earlier levels).  With two l-mers below the top, v must also
+// meet Lemma 1 for all four: Cd(x, u, top, v) <= 4d.  Returns false as soon as a row
+// empties (Section 2: "If any row becomes empty ... try a different l-mer").
 template <int NB, typename W, int T>
 __device__ bool filter_level(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &C, int k, int lane,
                              WarpCounters &wc)
@@ -181,6 +242,11 @@ __device__ bool filter_level(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &C, int
             dst[i] = diff(st[i], top);
         }
     }
+    // constants of the four-l-mer condition (stack x, u plus top), used when k == 2
+    const W lmask = low_mask<W>(I.l);
+    const W dxu = k >= 2 ? diff(st[0], st[1]) : W(0);
+    const W c4_none = k >= 2 ? dxu & dst[0] & dst[1] : W(0);   // x,u,top pairwise differ
+    const W c4_xuxt = k >= 2 ? dxu | dst[0] : W(0);             // x differs from u or top
     const uint32_t *in = C.lists + (size_t)(k - 2) * C.list_cap;
     uint32_t *out = C.lists + (size_t)(k - 1) * C.list_cap;
     const int br = S.brow[k];
@@ -204,12 +270,22 @@ __device__ bool filter_level(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &C, int
             const Lm<NB, W> v = C.lm[(size_t)row * I.L + (e & 0xFFFF)];
             const W dtv = diff(top, v);
             ok = popc(dtv) <= two_d;
+            W div[T];
 #pragma unroll
             for (int i = 0; i < T; i++) {
                 if (i < k) {
-                    const W div = diff(st[i], v);
-                    ok = ok && (popc(dst[i] | div) + popc(dst[i] & div & dtv) <= three_d);
+                    div[i] = diff(st[i], v);
+                    ok = ok && (popc(dst[i] | div[i]) + popc(dst[i] & div[i] & dtv) <= three_d);
                 }
+            }
+            if (T >= 4 && k == 2) {
+                // Lemma 1 for the four l-mers x, u, top, v: per column Cd contributes
+                // 3 - [some pair equal] - [some three equal] - [all four equal].
+                const W dxv = div[0], duv = div[1];
+                const W has2 = ~(c4_none & dxv & duv & dtv) & lmask;
+                const W has3 = ~(c4_xuxt & (dxu | dxv) & (dst[0] | dxv) & (dst[1] | duv)) & lmask;
+                const W all4 = ~(c4_xuxt | dxv) & lmask;
+                ok = ok && 3 * I.l - popc(has2) - popc(has3) - popc(all4) <= 4 * I.d;
             }
         }
         const unsigned bal = __ballot_sync(kFull, ok);
@@ -224,12 +300,12 @@ __device__ bool filter_level(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &C, int
         if (__any_sync(kFull, last && S.cnt[k + 1][row] == 0)) {
             const int done = c0 + 32 < total ? c0 + 32 : total;
             wc.compares += (unsigned long long)done * (k + 1);
-            wc.ops += (unsigned long long)done * op_filter(NB, k) * wscale<W>();
+            wc.ops += (unsigned long long)done * (op_filter(NB, k) + (T >= 4 && k == 2 ? op_lemma4() : 0)) * wscale<W>();
             return false;
         }
     }
     wc.compares += (unsigned long long)total * (k + 1);
-    wc.ops += (unsigned long long)total * op_filter(NB, k) * wscale<W>();
+    wc.ops += (unsigned long long)total * (op_filter(NB, k) + (T >= 4 && k == 2 ? op_lemma4() : 0)) * wscale<W>();
     if (lane == 0) {
         S.len[k + 1] = len;
         S.live[k + 1] = live1;
@@ -503,6 +579,7 @@ __device__ void enumerate(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &C, int k,
 // and a borrow-free byte compare tests them all against per-position limits at once:
 //   e_i <= d,   e_i + e_j <= 2d - Hd(T_i[q..], T_j[q..]),
 //   e_i + e_j + e_h <= 3d - Cd(T_i[q..], T_j[q..], T_h[q..])
+//   e_0 + e_1 + e_2 + e_3 <= 4d - Cd(T_0[q..], .., T_3[q..])        (four l-mers)
 // which is prune(T, r) of Algorithm 1 with r_i = d - e_i: the two-l-mer condition and
 // Lemma 1 on the suffix (Theorem 1 for three l-mers, Section 2.4).  The limits depend
 // only on the tuple and the prefix length q, so they are tabulated once per tuple.
@@ -561,8 +638,17 @@ __device__ bool tuple_table(const Lm<NB, W> (&st)[T], int tk, int l, int d, uint
 #pragma unroll
     for (int i = 0; i < T; i++)
         hs1[i] = hs2[i] = cs[i] = 0;
+    int cs4 = 0;   // Cd of the four l-mers over positions q.. (Lemma 1), when tk == 4
     bool ok = true;
     for (int q = l; q >= 0; q--) {
+        if (q < l && T >= 4 && tk == 4) {
+            const W d01 = dp[0][1], d02 = dp[0][2], d03 = dp[0][3];
+            const W d12 = dp[1][2], d13 = dp[1][3], d23 = dp[2][3];
+            const int has2 = (int)((~(d01 & d02 & d03 & d12 & d13 & d23) >> q) & 1);
+            const int has3 = (int)((~((d01 | d02) & (d01 | d03) & (d02 | d03) & (d12 | d13)) >> q) & 1);
+            const int all4 = (int)((~(d01 | d02 | d03) >> q) & 1);
+            cs4 += 3 - has2 - has3 - all4;
+        }
         if (q < l) {
 #pragma unroll
             for (int i = 0; i < T; i++) {
@@ -587,7 +673,7 @@ __device__ bool tuple_table(const Lm<NB, W> (&st)[T], int tk, int l, int d, uint
                 }
             }
         }
-        uint32_t lim1 = 0x7F7F7F7Fu, lim2 = 0x7F7F7F7Fu, lim3 = 0x7F7F7F7Fu, codes = 0;
+        uint32_t lim1 = 0x7F7F7F7Fu, lim2 = 0xFF7F7F7Fu, lim3 = 0x7F7F7F7Fu, codes = 0;
 #pragma unroll
         for (int i = 0; i < T; i++) {
             if (i < tk) {
@@ -611,6 +697,12 @@ __device__ bool tuple_table(const Lm<NB, W> (&st)[T], int tk, int l, int d, uint
                     codes |= (uint32_t)get_letter(st[i], q - 1) << sh;
             }
         }
+        if (T >= 4 && tk == 4) {
+            // pairs (i, i+2) repeat in bytes 2 and 3; byte 3 carries 4d - Cd(suffix)
+            const int v = 4 * d - cs4;
+            ok = ok && v >= 0;
+            lim2 = (lim2 & 0x00FFFFFFu) | ((uint32_t)(v < 0 ? 0 : v) << 24);
+        }
         tbl[q] = make_uint4(codes, lim1, lim2, lim3);
     }
     return ok;
@@ -619,7 +711,8 @@ __device__ bool tuple_table(const Lm<NB, W> (&st)[T], int tk, int l, int d, uint
 // Algorithm 1 + isMotif for up to four l-mers per tuple; arguments as in enumerate().
 template <int NB, typename W, int T>
 __device__ void enumerate_frontier(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &C, int k,
-                                   int br, int lane, WarpCounters &wc)
+                                   int br, int lane, WarpCounters &wc, int t_lo = 0,
+                                   int t_hi = 1 << 30, bool may_split = false, int p2 = -1)
 {
     static_assert(T <= 4, "the packed-byte frontier holds at most four budgets");
     const long long c_start = clock64();
@@ -647,12 +740,15 @@ __device__ void enumerate_frontier(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &
     const int chunk = K >= 32 ? 1 : 32 / K;   // nodes expanded per step
     const int my_node = lane / K, my_alpha = lane - (lane / K) * K;
     const uint32_t alpha_rep = (uint32_t)my_alpha * 0x01010101u;
-    wc.tuples += B;
+    wc.tuples += (t_hi < B ? t_hi : B) > t_lo ? (t_hi < B ? t_hi : B) - t_lo : 0;
     unsigned long long nodes = 0;
     int ncand = 0;
 
-    for (int base = 0; base < B; base += kTupleRound) {
-        const int nb = B - base < kTupleRound ? B - base : kTupleRound;
+    const int t_end = t_hi < B ? t_hi : B;
+    for (int base = t_lo; base < t_end; base += kTupleRound) {
+        if (may_split && base > t_lo && maybe_donate(C, base, t_end, lane, p2))
+            break;
+        const int nb = t_end - base < kTupleRound ? t_end - base : kTupleRound;
         // per-tuple tables, one tuple per lane
         bool root_ok = false;
         if (lane < nb) {
@@ -712,8 +808,10 @@ __device__ void enumerate_frontier(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &
                 const uint32_t s1 = e + __byte_perm(e, 0, r1);
                 const uint32_t s2 = e + __byte_perm(e, 0, r2);
                 const uint32_t s3 = s1 + __byte_perm(e, 0, r2);
-                ok = !(bytes_gt(e, lim0) | bytes_gt(s1, lim.y) | bytes_gt(s2, lim.z) |
-                       bytes_gt(s3, lim.w));
+                // byte 3 of lim.z bounds the sum of all budgets used (Lemma 1, four l-mers)
+                ok = !(bytes_gt(e, lim0) | bytes_gt(s1, lim.y) |
+                       bytes_gt(s2 & 0x00FFFFFFu, lim.z | 0x7F000000u) | bytes_gt(s3, lim.w) |
+                       (((e * 0x01010101u) >> 24) > (lim.z >> 24)));
                 child.M = nd.M;
                 set_letter(child.M, p, my_alpha);
                 child.e = e;
@@ -758,7 +856,7 @@ __device__ void enumerate_frontier(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &
     for (int o = 16; o > 0; o >>= 1)
         nodes += __shfl_xor_sync(kFull, nodes, o);
     wc.nodes += nodes;
-    wc.ops += nodes * (25ull + 2ull * NB * wscale<W>());
+    wc.ops += nodes * (op_child(NB) - 2ull * NB + 2ull * NB * wscale<W>());
     wc.cyc_enum += (clock64() - c_start) - (wc.cyc_verify - v_before);
 }
 
@@ -801,29 +899,50 @@ __device__ void run_item(WarpSm<NB, W, T> &S, SearchCtx<NB, W> &C, const Item &i
         enumerate_any(S, C, 2, -1, lane, wc);
         return;
     }
-    if (T == 3) {
-        enumerate_any(S, C, 2, choose_branch(S, 2, lane), lane, wc);
+    if constexpr (T == 3) {
+        enumerate_frontier(S, C, 2, choose_branch(S, 2, lane), lane, wc, it.lo,
+                           it.hi == kAllRange ? 1 << 30 : it.hi, true);
         return;
     }
     int k = 2;
-    {
-        const int b2 = choose_branch(S, 2, lane);
-        if (lane == 0) {
-            S.brow[2] = b2;
-            S.bpos[2] = 0;
+    const int b2 = choose_branch(S, 2, lane);
+    const int end2 = it.hi == kAllRange ? S.cnt[2][b2] : (it.hi < S.cnt[2][b2] ? it.hi : S.cnt[2][b2]);
+    if (lane == 0) {
+        S.brow[2] = b2;
+        S.bpos[2] = it.lo;
+    }
+    __syncwarp();
+    if constexpr (T == 4) {
+        if (it.hi3 != kAllRange) {
+            // one level-2 position and a range of the tuples below it
+            if (it.lo >= end2)
+                return;
+            const uint32_t e = C.lists[S.start[2][b2] + it.lo];
+            __syncwarp();
+            if (lane == 0) {
+                S.bpos[2] = it.lo + 1;
+                S.stk[2] = C.lm[(size_t)(e >> 16) * I.L + (e & 0xFFFF)];
+            }
+            __syncwarp();
+            if (!filter_level(S, C, 2, lane, wc) || S.live[3] == 0)
+                return;
+            enumerate_frontier(S, C, 3, choose_branch(S, 3, lane), lane, wc, it.lo3, it.hi3,
+                               true, it.lo);
+            return;
         }
-        __syncwarp();
     }
     for (;;) {
         // invariant: k < T-1 and the branch row of level k is chosen
         const int br = S.brow[k];
         const int pos = S.bpos[k];
-        if (pos >= S.cnt[k][br]) {
+        if (pos >= (k == 2 ? end2 : S.cnt[k][br])) {
             if (k == 2)
                 return;
             k--;
             continue;
         }
+        if (k == 2 && pos > it.lo && maybe_donate(C, pos, end2, lane))
+            return;
         const uint32_t e = C.lists[(size_t)(k - 2) * C.list_cap + S.start[k][br] + pos];
         __syncwarp();
         if (lane == 0) {
@@ -840,7 +959,11 @@ __device__ void run_item(WarpSm<NB, W, T> &S, SearchCtx<NB, W> &C, const Item &i
         if (S.live[k1] == 0) {
             enumerate_any(S, C, k1, -1, lane, wc);
         } else if (k1 == T - 1) {
-            enumerate_any(S, C, k1, choose_branch(S, k1, lane), lane, wc);
+            if constexpr (T == 4)
+                enumerate_frontier(S, C, k1, choose_branch(S, k1, lane), lane, wc, 0, 1 << 30,
+                                   true, pos);
+            else
+                enumerate_any(S, C, k1, choose_branch(S, k1, lane), lane, wc);
         } else {
             k = k1;
             const int nb = choose_branch(S, k, lane);
@@ -860,7 +983,8 @@ __global__ void __launch_bounds__(128, kSearchMinBlocks) search_kernel(
     unsigned long long *item_next, uint32_t *lists, uint64_t list_cap, uint64_t *keys,
     unsigned long long *key_count, uint64_t key_cap, int *status, DevStats *stats,
     int key_shift, int multi, unsigned char *fscr, uint64_t fscr_stride, int lmax,
-    int item_stride)
+    int item_stride, Item *donate, unsigned long long *donate_count, uint64_t donate_cap,
+    long long budget, ItemTrace *trace)
 {
     extern __shared__ unsigned char smem_raw[];
     WarpSm<NB, W, T> &S = reinterpret_cast<WarpSm<NB, W, T> *>(smem_raw)[threadIdx.x >> 5];
@@ -878,10 +1002,17 @@ __global__ void __launch_bounds__(128, kSearchMinBlocks) search_kernel(
     C.status = status;
     C.key_shift = key_shift;
     C.multi = multi;
+    C.donate = donate;
+    C.donate_count = donate_count;
+    C.donate_cap = donate_cap;
+    C.budget = budget;
     WarpCounters wc;
-    unsigned long long done = 0;
+    unsigned long long done = 0, item_max = 0;
+    const long long busy0 = clock64();
     const unsigned long long nall = *item_count < item_cap ? *item_count : item_cap;
     const unsigned long long nitems = (nall + item_stride - 1) / item_stride;
+    C.item_next = item_next;
+    C.nitems = nitems;
     for (;;) {
         unsigned long long it = 0;
         if (lane == 0)
@@ -893,7 +1024,15 @@ __global__ void __launch_bounds__(128, kSearchMinBlocks) search_kernel(
         C.I = inst + item.inst;
         C.inst = (int)item.inst;
         C.lm = lmers + C.I->lmer_off;
+        const long long it0 = __shfl_sync(kFull, clock64(), 0);
+        C.item = item;
+        C.t0 = it0;
+        const unsigned long long n0 = wc.nodes, l0 = wc.leaves, t0 = wc.tuples;
         run_item(S, C, item, lane, wc);
+        const unsigned long long dt = (unsigned long long)(clock64() - it0);
+        if (trace && lane == 0)
+            trace[it] = ItemTrace{item, dt, wc.nodes - n0, wc.leaves - l0, wc.tuples - t0};
+        item_max = dt > item_max ? dt : item_max;
         done++;
         __syncwarp();
     }
@@ -908,6 +1047,11 @@ __global__ void __launch_bounds__(128, kSearchMinBlocks) search_kernel(
         atomicAdd(&stats->cyc_enum, (unsigned long long)wc.cyc_enum);
         atomicAdd(&stats->cyc_verify, (unsigned long long)wc.cyc_verify);
         atomicAdd(&stats->search_ops, wc.ops);
+        const unsigned long long busy = (unsigned long long)(clock64() - busy0);
+        atomicMax(&stats->busy_max, busy);
+        atomicAdd(&stats->busy_sum, busy);
+        atomicAdd(&stats->warps, 1ull);
+        atomicMax(&stats->item_max, item_max);
     }
 }
 
@@ -928,7 +1072,8 @@ cudaError_t launch(const SearchArgs &a, cudaStream_t s)
     search_kernel<NB, W, T><<<a.cfg.blocks, a.cfg.warps_per_block * 32, smem, s>>>(
         a.inst, static_cast<const Lm<NB, W> *>(a.lmers), a.items, a.item_count, a.item_cap,
         a.item_next, a.lists, a.list_cap, a.keys, a.key_count, a.key_cap, a.status, a.stats,
-        a.key_shift, a.multi, a.fscr, a.fscr_stride, a.lmax, a.item_stride > 0 ? a.item_stride : 1);
+        a.key_shift, a.multi, a.fscr, a.fscr_stride, a.lmax, a.item_stride > 0 ? a.item_stride : 1,
+        a.donate, a.donate_count, a.donate_cap, a.budget, a.trace);
     return cudaGetLastError();
 }
 

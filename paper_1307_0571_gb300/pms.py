@@ -54,7 +54,9 @@ class pms_stats(ctypes.Structure):
                 ("leaves", ctypes.c_uint64), ("raw_motifs", ctypes.c_uint64),
                 ("cyc_filter", ctypes.c_uint64), ("cyc_enum", ctypes.c_uint64),
                 ("cyc_verify", ctypes.c_uint64), ("search_ops", ctypes.c_uint64),
-                ("launches", ctypes.c_uint64), ("h2d_bytes", ctypes.c_uint64),
+                ("launches", ctypes.c_uint64), ("busy_max", ctypes.c_uint64),
+                ("busy_mean", ctypes.c_uint64), ("item_max", ctypes.c_uint64),
+                ("h2d_bytes", ctypes.c_uint64),
                 ("d2h_bytes", ctypes.c_uint64), ("kernel_ms", ctypes.c_double),
                 ("search_ms", ctypes.c_double),
                 ("threshold", ctypes.c_int)]
