@@ -79,6 +79,8 @@ typedef struct pms_instance {
     int n, m;
     const char *alphabet;     /* NUL-terminated */
     int l, d;
+    int x_begin, x_end;       /* subproblems of the l-mers x_begin..x_end-1 of S_1 only
+                                 (Section 2.3); both 0 = the context's range (all) */
 } pms_instance;
 
 /* Counters of one solve, summed over the kernels that ran. */

@@ -96,12 +96,12 @@ struct Workspace {
     cudaStream_t stream = nullptr;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     DBuf seqs, maps, inst, alpha, lmers, items, lists, fscr, keys, keys_alt, hist, flags,
-        out_chars, byte_off, first, last, counters, don0, don1, trace;
+        out_chars, byte_off, first, last, counters, don0, don1, trace, planes;
     std::vector<DBuf *> all()
     {
         return {&seqs, &maps, &inst, &alpha, &lmers, &items, &lists, &fscr, &keys, &keys_alt,
                 &hist, &flags, &out_chars, &byte_off, &first, &last, &counters, &don0, &don1,
-                &trace};
+                &trace, &planes};
     }
 };
 
@@ -227,6 +227,7 @@ struct Request {
     uint64_t ticket;
     std::string seqs, alphabet;
     int n, m, l, d;
+    int x_begin, x_end;
     std::chrono::steady_clock::time_point arrival;
 };
 
@@ -417,6 +418,8 @@ int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
         const uint64_t nw = (uint64_t)cf.blocks * cf.warps_per_block;
         int rc = w.lists.ensure(4ull * nw * search_levels(tt) * list_cap, c->held);
         if (rc == PMS_OK)
+            rc = w.planes.ensure(lmer_bytes(lay) * nw * search_levels(tt) * list_cap, c->held);
+        if (rc == PMS_OK)
             rc = w.fscr.ensure(fstride * nw, c->held);
         return rc;
     };
@@ -486,7 +489,8 @@ int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
                           &dc->key_count, key_cap, &dc->status, &dc->stats, key_bits, multi,
                           cf, w.fscr.as<unsigned char>(), fstride, lmax,
                           first_pass ? stride : 1, don[out], &dc->donate_count[out],
-                          kDonateCap, kItemBudget, first_pass ? trace : nullptr};
+                          kDonateCap, kItemBudget, first_pass ? trace : nullptr,
+                          w.planes.p};
             PMS_CU(launch_search(lay, tt, sa, s));
             launches++;
             unsigned long long handed = 0;
@@ -807,9 +811,13 @@ void serve_worker(pms_ctx *c, Workspace *w)
         std::vector<Prep> ok_ins;
         std::vector<int> ok_idx;
         for (size_t i = 0; i < batch.size(); i++) {
+            pms_opts o = c->opts;
+            if (batch[i].x_begin || batch[i].x_end) {
+                o.x_begin = batch[i].x_begin;
+                o.x_end = batch[i].x_end;
+            }
             pre_rc[i] = prepare(batch[i].seqs.data(), batch[i].n, batch[i].m,
-                                batch[i].alphabet.c_str(), batch[i].l, batch[i].d, c->opts,
-                                ins[i]);
+                                batch[i].alphabet.c_str(), batch[i].l, batch[i].d, o, ins[i]);
             if (pre_rc[i] == PMS_OK) {
                 ok_ins.push_back(ins[i]);
                 ok_idx.push_back((int)i);
@@ -948,7 +956,7 @@ int pms_solve(pms_ctx *c, const char *seqs, int n, int m, const char *alphabet, 
 {
     if (!c || !out)
         return PMS_E_INVAL;
-    pms_instance in{seqs, n, m, alphabet, l, d};
+    pms_instance in{seqs, n, m, alphabet, l, d, 0, 0};
     return pms_solve_batch(c, &in, 1, out);
 }
 
@@ -959,8 +967,13 @@ int pms_solve_batch(pms_ctx *c, const pms_instance *inst, int count, pms_result 
     std::vector<Prep> ins(count);
     for (int i = 0; i < count; i++) {
         outs[i] = pms_result{};
+        pms_opts o = c->opts;
+        if (inst[i].x_begin || inst[i].x_end) {
+            o.x_begin = inst[i].x_begin;
+            o.x_end = inst[i].x_end;
+        }
         int rc = prepare(inst[i].seqs, inst[i].n, inst[i].m, inst[i].alphabet, inst[i].l,
-                         inst[i].d, c->opts, ins[i]);
+                         inst[i].d, o, ins[i]);
         if (rc != PMS_OK)
             return rc;
     }
@@ -1034,6 +1047,8 @@ int pms_submit(pms_ctx *c, const pms_instance *inst, uint64_t *ticket)
     r.m = inst->m;
     r.l = inst->l;
     r.d = inst->d;
+    r.x_begin = inst->x_begin;
+    r.x_end = inst->x_end;
     r.arrival = std::chrono::steady_clock::now();
     {
         std::lock_guard<std::mutex> lk(c->q_mu);

@@ -159,9 +159,11 @@ struct SearchArgs {
     uint64_t donate_cap;
     long long budget;         // cycles an item runs before it hands on the rest of its range
     ItemTrace *trace;         // per-item records of the first pass, or null
+    void *planes;             // scratch: the l-mers of the list entries (same shape as lists)
 };
 
-// Lists each search warp keeps for threshold t (levels 2..t-1, at least one).
+// Lists each search warp keeps for threshold t (levels 2..t-1, at least one).  Every list
+// entry is 4 bytes of (string, position) in `lists` plus the l-mer itself in `planes`.
 inline int search_levels(int t) { return t > 2 ? t - 2 : 1; }
 
 // The stack search + enumeration + verification (Algorithm 2 with Algorithm 1),

@@ -179,12 +179,12 @@ int solve_noalloc(const char *d_seqs, int n, int m, const char *alphabet, int l,
     if (off + 1024 >= kNoAllocScratch)
         return PMS_E_NOMEM;
     const uint64_t fstride = up256(search_frontier_bytes(lay, l));
-    const uint64_t per_warp = 4ull * search_levels(t) * list_cap + fstride;
+    const uint64_t per_warp = (4ull + na_lmer_bytes(lay)) * search_levels(t) * list_cap + fstride;
     const int wpb = 4;
     int per_sm = search_max_blocks(lay, t, wpb);
     if (per_sm <= 0)
         return PMS_E_CUDA;
-    // leave room for the 256-byte rounding of the two regions below
+    // leave room for the 256-byte rounding of the three regions below
     uint64_t blocks = (kNoAllocScratch - off - 1024) / (per_warp * wpb);
     if (blocks > (uint64_t)per_sm * sms)
         blocks = (uint64_t)per_sm * sms;
@@ -192,6 +192,7 @@ int solve_noalloc(const char *d_seqs, int n, int m, const char *alphabet, int l,
         return PMS_E_NOMEM;   // too little scratch left for a useful search grid
     const uint64_t nwarps = blocks * wpb;
     const size_t o_lists = take(4ull * nwarps * search_levels(t) * list_cap);
+    const size_t o_planes = take(na_lmer_bytes(lay) * nwarps * search_levels(t) * list_cap);
     const size_t o_fscr = take(fstride * nwarps);
     if (off > kNoAllocScratch)
         return PMS_E_NOMEM;
@@ -234,7 +235,7 @@ int solve_noalloc(const char *d_seqs, int n, int m, const char *alphabet, int l,
                   reinterpret_cast<uint64_t *>(base + o_keys), &dc->key_count, kNoAllocRawKeys,
                   &dc->status, &dc->stats, l * kbits, 0,
                   LaunchCfg{wpb, (int)blocks}, base + o_fscr, fstride, l, 1, nullptr, nullptr,
-                  0, 0, nullptr};
+                  0, 0, nullptr, base + o_planes};
     NA_CU(launch_search(lay, t, sa, s));
     NaCounters hc;
     NA_CU(cudaMemcpyAsync(&hc, dc, sizeof hc, cudaMemcpyDeviceToHost, s));

@@ -63,6 +63,7 @@ struct SearchCtx {
     int inst;
     const Lm<NB, W> *lm;      // this instance's l-mer table
     uint32_t *lists;          // this warp's lists; level k at (k-2)*list_cap
+    Lm<NB, W> *planes;        // the l-mers of those list entries, same indexing
     uint64_t list_cap;
     unsigned char *fscr;      // this warp's frontier-enumeration scratch
     int lmax;                 // longest l of the batch (sizes fscr's table)
@@ -182,6 +183,7 @@ __device__ bool build_level2(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &C, int
     const W dxu = diff(x, u);
     const int two_d = 2 * I.d, three_d = 3 * I.d;
     uint32_t *out = C.lists;
+    Lm<NB, W> *out_lm = C.planes;
     int len = 0;
     uint64_t live = 0;
     for (int r = 1; r < I.n; r++) {
@@ -192,15 +194,19 @@ __device__ bool build_level2(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &C, int
         for (int j0 = 0; j0 < I.L; j0 += 32) {
             const int j = j0 + lane;
             bool ok = false;
+            Lm<NB, W> v;
             if (j < I.L) {
-                const Lm<NB, W> v = row[j];
+                v = row[j];
                 const W dxv = diff(x, v), duv = diff(u, v);
                 ok = popc(dxv) <= two_d && popc(duv) <= two_d &&
                      popc(dxu | dxv) + popc(dxu & dxv & duv) <= three_d;
             }
             const unsigned bal = __ballot_sync(kFull, ok);
-            if (ok)
-                out[len + __popc(bal & lanemask_lt())] = ((uint32_t)r << 16) | (uint32_t)j;
+            if (ok) {
+                const int at = len + __popc(bal & lanemask_lt());
+                out[at] = ((uint32_t)r << 16) | (uint32_t)j;
+                out_lm[at] = v;
+            }
             len += __popc(bal);
         }
         wc.compares += 3ull * I.L;
@@ -249,6 +255,8 @@ __device__ bool filter_level(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &C, int
     const W c4_xuxt = k >= 2 ? dxu | dst[0] : W(0);             // x differs from u or top
     const uint32_t *in = C.lists + (size_t)(k - 2) * C.list_cap;
     uint32_t *out = C.lists + (size_t)(k - 1) * C.list_cap;
+    const Lm<NB, W> *in_lm = C.planes + (size_t)(k - 2) * C.list_cap;
+    Lm<NB, W> *out_lm = C.planes + (size_t)(k - 1) * C.list_cap;
     const int br = S.brow[k];
     const int bs = S.start[k][br], bc = S.cnt[k][br];
     const int total = S.len[k] - bc;
@@ -264,10 +272,11 @@ __device__ bool filter_level(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &C, int
         bool ok = false;
         int row = -1;
         uint32_t e = 0;
+        Lm<NB, W> v;
         if (valid) {
             e = in[idx];
+            v = in_lm[idx];
             row = (int)(e >> 16);
-            const Lm<NB, W> v = C.lm[(size_t)row * I.L + (e & 0xFFFF)];
             const W dtv = diff(top, v);
             ok = popc(dtv) <= two_d;
             W div[T];
@@ -289,8 +298,11 @@ __device__ bool filter_level(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &C, int
             }
         }
         const unsigned bal = __ballot_sync(kFull, ok);
-        if (ok)
-            out[len + __popc(bal & lanemask_lt())] = e;
+        if (ok) {
+            const int at = len + __popc(bal & lanemask_lt());
+            out[at] = e;
+            out_lm[at] = v;
+        }
         len += __popc(bal);
         const unsigned grp = __match_any_sync(kFull, row);
         if (valid && lane == __ffs(grp) - 1)
@@ -396,16 +408,15 @@ __device__ void verify_and_emit(const WarpSm<NB, W, T> &S, const SearchCtx<NB, W
     const InstDesc &I = *C.I;
     const Lm<NB, W> M = S.cand[lane < ncand ? lane : 0];
     bool alive = lane < ncand;
-    const uint32_t *list = k >= 2 ? C.lists + (size_t)(k - 2) * C.list_cap : C.lists;
+    const Lm<NB, W> *list_lm = k >= 2 ? C.planes + (size_t)(k - 2) * C.list_cap : C.planes;
     while (rows && __any_sync(kFull, alive)) {
         const int r = __ffsll((long long)rows) - 1;
         rows &= rows - 1;
         const int s0 = S.start[k][r], c = S.cnt[k][r];
-        const Lm<NB, W> *row = C.lm + (size_t)r * I.L;
         bool hit = false;
         const int nalive = __popc(__ballot_sync(kFull, alive));
         for (int j0 = 0; j0 < c; j0 += 32) {
-            const Lm<NB, W> vj = row[j0 + lane < c ? (list[s0 + j0 + lane] & 0xFFFF) : 0];
+            const Lm<NB, W> vj = list_lm[s0 + (j0 + lane < c ? j0 + lane : 0)];
             const int jn = c - j0 < 32 ? c - j0 : 32;
             for (int jj = 0; jj < jn; jj++) {
                 const Lm<NB, W> v = shfl_lm(vj, jj);
@@ -470,9 +481,8 @@ __device__ void enumerate(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &C, int k,
                 dp[i][j] = diff(st[i], st[j]);
 
     const int B = branch ? S.cnt[k][br] : 1;
-    const uint32_t *blist = branch ? C.lists + (size_t)(k - 2) * C.list_cap + S.start[k][br]
-                                   : C.lists;
-    const Lm<NB, W> *brow_lm = C.lm + (size_t)(branch ? br : 0) * I.L;
+    const Lm<NB, W> *blist_lm =
+        branch ? C.planes + (size_t)(k - 2) * C.list_cap + S.start[k][br] : C.planes;
     int P = 0, U = 1;
     while (P < l && B * U < 64) {
         P++;
@@ -510,7 +520,7 @@ __device__ void enumerate(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &C, int k,
                 const int tb = unit / U;
                 int code = unit - tb * U;
                 if (branch) {
-                    st[T - 1] = brow_lm[blist[tb] & 0xFFFF];
+                    st[T - 1] = blist_lm[tb];
 #pragma unroll
                     for (int i = 0; i < T - 1; i++)
                         dp[i][T - 1] = diff(st[i], st[T - 1]);
@@ -726,9 +736,8 @@ __device__ void enumerate_frontier(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &
     FNode<NB, W> *const front = reinterpret_cast<FNode<NB, W> *>(
         C.fscr + (size_t)kTupleRound * (C.lmax + 1) * sizeof(uint4));
     const int B = branch ? S.cnt[k][br] : 1;
-    const uint32_t *blist = branch ? C.lists + (size_t)(k - 2) * C.list_cap + S.start[k][br]
-                                   : C.lists;
-    const Lm<NB, W> *brow_lm = C.lm + (size_t)(branch ? br : 0) * I.L;
+    const Lm<NB, W> *blist_lm =
+        branch ? C.planes + (size_t)(k - 2) * C.list_cap + S.start[k][br] : C.planes;
 
     uint32_t r1, r2;
     rot_selectors(tk, r1, r2);
@@ -758,7 +767,7 @@ __device__ void enumerate_frontier(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &
                 if (i < k)
                     st[i] = S.stk[i];
             if (branch)
-                st[T - 1] = brow_lm[blist[base + lane] & 0xFFFF];
+                st[T - 1] = blist_lm[base + lane];
             root_ok = tuple_table<NB, W, T>(st, tk, l, d, tbl_all + (size_t)lane * (l + 1));
         }
         __syncwarp();
@@ -917,11 +926,11 @@ __device__ void run_item(WarpSm<NB, W, T> &S, SearchCtx<NB, W> &C, const Item &i
             // one level-2 position and a range of the tuples below it
             if (it.lo >= end2)
                 return;
-            const uint32_t e = C.lists[S.start[2][b2] + it.lo];
+            const Lm<NB, W> e = C.planes[S.start[2][b2] + it.lo];
             __syncwarp();
             if (lane == 0) {
                 S.bpos[2] = it.lo + 1;
-                S.stk[2] = C.lm[(size_t)(e >> 16) * I.L + (e & 0xFFFF)];
+                S.stk[2] = e;
             }
             __syncwarp();
             if (!filter_level(S, C, 2, lane, wc) || S.live[3] == 0)
@@ -943,11 +952,11 @@ __device__ void run_item(WarpSm<NB, W, T> &S, SearchCtx<NB, W> &C, const Item &i
         }
         if (k == 2 && pos > it.lo && maybe_donate(C, pos, end2, lane))
             return;
-        const uint32_t e = C.lists[(size_t)(k - 2) * C.list_cap + S.start[k][br] + pos];
+        const Lm<NB, W> e = C.planes[(size_t)(k - 2) * C.list_cap + S.start[k][br] + pos];
         __syncwarp();
         if (lane == 0) {
             S.bpos[k] = pos + 1;
-            S.stk[k] = C.lm[(size_t)(e >> 16) * I.L + (e & 0xFFFF)];
+            S.stk[k] = e;
         }
         __syncwarp();
         c0 = clock64();
@@ -984,7 +993,7 @@ __global__ void __launch_bounds__(128, kSearchMinBlocks) search_kernel(
     unsigned long long *key_count, uint64_t key_cap, int *status, DevStats *stats,
     int key_shift, int multi, unsigned char *fscr, uint64_t fscr_stride, int lmax,
     int item_stride, Item *donate, unsigned long long *donate_count, uint64_t donate_cap,
-    long long budget, ItemTrace *trace)
+    long long budget, ItemTrace *trace, void *planes)
 {
     extern __shared__ unsigned char smem_raw[];
     WarpSm<NB, W, T> &S = reinterpret_cast<WarpSm<NB, W, T> *>(smem_raw)[threadIdx.x >> 5];
@@ -993,6 +1002,7 @@ __global__ void __launch_bounds__(128, kSearchMinBlocks) search_kernel(
     constexpr int levels = T > 2 ? T - 2 : 1;
     SearchCtx<NB, W> C;
     C.lists = lists + gw * (uint64_t)levels * list_cap;
+    C.planes = static_cast<Lm<NB, W> *>(planes) + gw * (uint64_t)levels * list_cap;
     C.list_cap = list_cap;
     C.fscr = fscr + gw * fscr_stride;
     C.lmax = lmax;
@@ -1073,7 +1083,7 @@ cudaError_t launch(const SearchArgs &a, cudaStream_t s)
         a.inst, static_cast<const Lm<NB, W> *>(a.lmers), a.items, a.item_count, a.item_cap,
         a.item_next, a.lists, a.list_cap, a.keys, a.key_count, a.key_cap, a.status, a.stats,
         a.key_shift, a.multi, a.fscr, a.fscr_stride, a.lmax, a.item_stride > 0 ? a.item_stride : 1,
-        a.donate, a.donate_count, a.donate_cap, a.budget, a.trace);
+        a.donate, a.donate_count, a.donate_cap, a.budget, a.trace, a.planes);
     return cudaGetLastError();
 }
 

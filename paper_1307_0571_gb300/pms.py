@@ -45,7 +45,8 @@ class pms_opts(ctypes.Structure):
 
 class pms_instance(ctypes.Structure):
     _fields_ = [("seqs", ctypes.c_char_p), ("n", ctypes.c_int), ("m", ctypes.c_int),
-                ("alphabet", ctypes.c_char_p), ("l", ctypes.c_int), ("d", ctypes.c_int)]
+                ("alphabet", ctypes.c_char_p), ("l", ctypes.c_int), ("d", ctypes.c_int),
+                ("x_begin", ctypes.c_int), ("x_end", ctypes.c_int)]
 
 
 class pms_stats(ctypes.Structure):
@@ -145,6 +146,8 @@ class Instance:
     alphabet: str
     l: int
     d: int
+    x_begin: int = 0        # subproblems of l-mers x_begin..x_end-1 of S_1; 0, 0 = all
+    x_end: int = 0
 
 
 def _b(x) -> bytes:
@@ -223,7 +226,7 @@ class Context:
         for i, it in enumerate(insts):
             s, a = _b(it.seqs), it.alphabet.encode("ascii")
             keep += [s, a]
-            arr[i] = pms_instance(s, it.n, it.m, a, it.l, it.d)
+            arr[i] = pms_instance(s, it.n, it.m, a, it.l, it.d, it.x_begin, it.x_end)
         outs = (pms_result * len(insts))()
         rc = self.lib.pms_solve_batch(self.h, arr, len(insts), outs)
         if rc != PMS_OK:
@@ -248,7 +251,7 @@ class Context:
 
     def submit(self, it: Instance) -> int:
         s, a = _b(it.seqs), it.alphabet.encode("ascii")
-        inst = pms_instance(s, it.n, it.m, a, it.l, it.d)
+        inst = pms_instance(s, it.n, it.m, a, it.l, it.d, it.x_begin, it.x_end)
         t = ctypes.c_uint64(0)
         rc = self.lib.pms_submit(self.h, ctypes.byref(inst), ctypes.byref(t))
         if rc != PMS_OK:

@@ -18,3 +18,13 @@ def oracle_lib():
     import oracle
     oracle.build()
     return oracle
+
+
+def golden_module():
+    """tests/golden/make_golden.py as a module (stored oracle sets and their readers)."""
+    import importlib.util
+    path = os.path.join(ROOT, "tests", "golden", "make_golden.py")
+    spec = importlib.util.spec_from_file_location("make_golden", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
