@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libpms.so")
 SOURCES = ["pms_prep.cu", "pms_search_dna32.cu", "pms_search_dna64.cu", "pms_search_p5_32.cu",
-           "pms_search_p5_64.cu", "pms_sort.cu", "pms_api.cu", "pms_noalloc.cu"]
+           "pms_sort.cu", "pms_api.cu", "pms_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

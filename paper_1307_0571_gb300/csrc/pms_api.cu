@@ -89,6 +89,9 @@ struct Counters {           // one device block of small counters
 // (100x the median) would otherwise set, without repeating work earlier in the pass.
 constexpr uint64_t kDonateCap = 1u << 20;
 constexpr long long kItemBudget = 4000000;
+// Autotuning: an item running longer than this (cycles, ~10 ms) stops and marks the
+// candidate threshold as capped.
+constexpr long long kTuneItemCap = 20000000;
 
 // Everything one pipeline run needs on the device; a context owns one for blocking calls
 // and one per serving slot, so slots run concurrently on their own streams.
@@ -105,10 +108,21 @@ struct Workspace {
     }
 };
 
+// A failing CUDA call returns PMS_E_CUDA; with PMS_DEBUG set in the environment the
+// call, its place and CUDA's error string also go to stderr.
+void report_cuda(cudaError_t e, const char *what, int line)
+{
+    static const bool on = std::getenv("PMS_DEBUG") != nullptr;
+    if (on)
+        std::fprintf(stderr, "libpms: %s failed at pms_api.cu:%d: %s (%d)\n", what, line,
+                     cudaGetErrorString(e), (int)e);
+}
+
 #define PMS_CU(call)                               \
     do {                                           \
         cudaError_t e_ = (call);                   \
         if (e_ != cudaSuccess) {                   \
+            report_cuda(e_, #call, __LINE__);      \
             cudaGetLastError();                    \
             return PMS_E_CUDA;                     \
         }                                          \
@@ -196,23 +210,31 @@ double nbhd(int l, int d, int k)
 // Appendix D: with p = N_2d/|S|^l (chance that an l-mer survives the 2d filter of the
 // stack top) and q = N_d/N_2d, the sample-driven part costs
 // Time_s(t) = n l sum_{j<=t} L^j p^{j(j-1)/2} and the pattern-driven part
-// Time_p(t) = L^t p^{t(t-1)/2} N_d q^{t-1} l; t minimises their sum over 2..min(n, 8).
-int model_threshold(int n, int m, int l, int d, int k)
+// Time_p(t) = L^t p^{t(t-1)/2} N_d q^{t-1} l.
+double model_cost(int n, int m, int l, int d, int k, int t)
 {
     const double L = m - l + 1;
     const double nd = nbhd(l, d, k), n2d = nbhd(l, 2 * d, k);
     const double total = std::pow((double)k, l);
     const double p = std::min(1.0, n2d / total), q = std::min(1.0, nd / std::max(n2d, 1.0));
+    double ts = 0;
+    for (int j = 1; j <= t; j++)
+        ts += std::pow(L, j) * std::pow(p, j * (j - 1) / 2.0);
+    ts *= (double)n * l;
+    const double tp =
+        std::pow(L, t) * std::pow(p, t * (t - 1) / 2.0) * nd * std::pow(q, t - 1) * l;
+    return ts + tp;
+}
+
+// The t in 2..min(n, 8) that minimises the Appendix D cost.
+int model_threshold(int n, int m, int l, int d, int k)
+{
     int best = 2;
     double best_cost = INFINITY;
     for (int t = 2; t <= std::min(n, kTMax); t++) {
-        double ts = 0;
-        for (int j = 1; j <= t; j++)
-            ts += std::pow(L, j) * std::pow(p, j * (j - 1) / 2.0);
-        ts *= (double)n * l;
-        double tp = std::pow(L, t) * std::pow(p, t * (t - 1) / 2.0) * nd * std::pow(q, t - 1) * l;
-        if (ts + tp < best_cost) {
-            best_cost = ts + tp;
+        const double cost = model_cost(n, m, l, d, k, t);
+        if (cost < best_cost) {
+            best_cost = cost;
             best = t;
         }
     }
@@ -472,7 +494,7 @@ int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
     }
     // The search: pass 0 over the items, then passes over the items handed on by
     // subproblems that ran past their budget, until none are.
-    auto search = [&](int tt, const LaunchCfg &cf, int stride) -> int {
+    auto search = [&](int tt, const LaunchCfg &cf, int stride, long long cap = 0) -> int {
         Item *don[2] = {w.don0.as<Item>(), w.don1.as<Item>()};
         for (int pass = 0;; pass++) {
             const bool first_pass = pass == 0;
@@ -489,8 +511,10 @@ int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
                           &dc->key_count, key_cap, &dc->status, &dc->stats, key_bits, multi,
                           cf, w.fscr.as<unsigned char>(), fstride, lmax,
                           first_pass ? stride : 1, don[out], &dc->donate_count[out],
-                          kDonateCap, kItemBudget, first_pass ? trace : nullptr,
-                          w.planes.p};
+                          cap ? 0 : kDonateCap, cap ? cap : kItemBudget,
+                          first_pass ? trace : nullptr, w.planes.p, cap ? 1 : 0};
+            if (cap)
+                sa.donate = nullptr;
             PMS_CU(launch_search(lay, tt, sa, s));
             launches++;
             unsigned long long handed = 0;
@@ -508,24 +532,33 @@ int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
         PMS_CU(copy(&nitems, &dc->item_count, sizeof nitems, cudaMemcpyDeviceToHost, s));
         PMS_CU(cudaStreamSynchronize(s));
         const int stride = (int)std::max<unsigned long long>(1, nitems / 1024);
+        // The first candidate runs under a generous safety cap; each later one is capped at
+        // 4x the slowest item of the best uncapped candidate so far, and a capped candidate
+        // is out (some item of it ran far longer than that item).
         float best_ms = INFINITY;
+        unsigned long long best_item = 0;
         tune->ms.clear();
         for (int tt : tune->cand) {
             LaunchCfg cf{};
             PMS_TRY(shape(tt, cf));
             PMS_TRY(scratch(tt, cf));
-            unsigned long long zero[2] = {0, 0};
-            PMS_CU(cudaMemcpyAsync(&dc->item_next, zero, 16, cudaMemcpyHostToDevice, s));
+            const long long cap = tune->best ? std::max<long long>(kTuneItemCap, 4 * (long long)best_item)
+                                             : 8 * kTuneItemCap;
             PMS_CU(cudaMemsetAsync(&dc->status, 0, sizeof(int), s));
+            PMS_CU(cudaMemsetAsync(&dc->stats, 0, sizeof(DevStats), s));
             PMS_CU(cudaEventRecord(w.ev[1], s));
-            PMS_TRY(search(tt, cf, stride));
+            PMS_TRY(search(tt, cf, stride, cap));
             PMS_CU(cudaEventRecord(w.ev[2], s));
+            Counters tc{};
+            PMS_CU(cudaMemcpyAsync(&tc, dc, sizeof tc, cudaMemcpyDeviceToHost, s));
             PMS_CU(cudaStreamSynchronize(s));
             float ms = 0;
             cudaEventElapsedTime(&ms, w.ev[1], w.ev[2]);
-            tune->ms.push_back(ms);
-            if (ms < best_ms) {
+            const bool capped = (tc.status & kErrTuneCapped) != 0;
+            tune->ms.push_back(capped ? INFINITY : ms);
+            if (!capped && ms < best_ms) {
                 best_ms = ms;
+                best_item = tc.stats.item_max;
                 tune->best = tt;
             }
         }
@@ -539,8 +572,14 @@ int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
         PMS_CU(cudaStreamSynchronize(s));
         if (hc.status & kErrAlphabet)
             return PMS_E_ALPHABET;
-        if (hc.status & kErrItemsOverflow)
+        if (hc.status & kErrItemsOverflow) {
+            report_cuda(cudaErrorUnknown, "item list overflow", __LINE__);
             return PMS_E_CUDA;
+        }
+        if (hc.status & kErrBounds) {
+            report_cuda(cudaErrorUnknown, "search index check", (int)hc.stats.bad_site);
+            return PMS_E_CUDA;
+        }
         if (!(hc.status & kErrKeysOverflow))
             break;
         // the raw (not yet unique) motif list outgrew its buffer: grow and search again
@@ -690,9 +729,19 @@ void autotune(pms_ctx *c, Workspace &w, const Prep &p)
     const int model = model_threshold(p.n, p.m, p.l, p.d, p.k);
     const int hi = std::min(p.n, kTMax);
     Tune tu;
+    // candidates: thresholds around the model's, the most often best one (4) first (tuning
+    // passes stop any item that runs past a cycle cap, so a candidate whose
+    // neighbourhoods explode costs little)
+    std::vector<int> around;
     for (int t = std::max(2, std::min(model - 1, 3)); t <= std::min(hi, std::max(model + 1, 5));
          t++)
         if (!(p.d > 41 && t < 5))
+            around.push_back(t);
+    for (int t : around)
+        if (t == 4)
+            tu.cand.push_back(t);
+    for (int t : around)
+        if (t != 4)
             tu.cand.push_back(t);
     int chosen = model;
     if (tu.cand.size() > 1 && p.n >= 3) {

@@ -75,6 +75,8 @@ struct DevStats {
     unsigned long long busy_sum;     // per-warp busy time summed over warps
     unsigned long long warps;        // warps of the search launch
     unsigned long long item_max;     // most cycles one item took
+    unsigned long long bad_site;     // PMS_BOUNDS_CHECK builds: first failing check's line
+    unsigned long long bad_value;    // ... and the index it saw
 };
 
 // Algorithmic integer-op counts per unit of work, for NB planes of 32-bit words (64-bit
@@ -109,6 +111,8 @@ enum : int {
     kErrItemsOverflow = 2,
     kErrKeysOverflow = 4,
     kErrListOverflow = 8,
+    kErrTuneCapped = 16,      // an autotuning pass stopped an item at its cycle cap
+    kErrBounds = 32,          // PMS_BOUNDS_CHECK builds: an index failed its check
 };
 
 // Plane layout classes: bits per letter (2 for |alphabet| <= 4, else 5) and word width.
@@ -160,6 +164,7 @@ struct SearchArgs {
     long long budget;         // cycles an item runs before it hands on the rest of its range
     ItemTrace *trace;         // per-item records of the first pass, or null
     void *planes;             // scratch: the l-mers of the list entries (same shape as lists)
+    int tune_cap;             // autotuning: stop any item still running after `budget`
 };
 
 // Lists each search warp keeps for threshold t (levels 2..t-1, at least one).  Every list

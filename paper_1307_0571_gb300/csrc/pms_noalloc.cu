@@ -235,7 +235,7 @@ int solve_noalloc(const char *d_seqs, int n, int m, const char *alphabet, int l,
                   reinterpret_cast<uint64_t *>(base + o_keys), &dc->key_count, kNoAllocRawKeys,
                   &dc->status, &dc->stats, l * kbits, 0,
                   LaunchCfg{wpb, (int)blocks}, base + o_fscr, fstride, l, 1, nullptr, nullptr,
-                  0, 0, nullptr, base + o_planes};
+                  0, 0, nullptr, base + o_planes, 0};
     NA_CU(launch_search(lay, t, sa, s));
     NaCounters hc;
     NA_CU(cudaMemcpyAsync(&hc, dc, sizeof hc, cudaMemcpyDeviceToHost, s));

@@ -183,15 +183,12 @@ namespace pms {
 cudaError_t launch_search_dna32(int t, const SearchArgs &a, cudaStream_t s);
 cudaError_t launch_search_dna64(int t, const SearchArgs &a, cudaStream_t s);
 cudaError_t launch_search_p5_32(int t, const SearchArgs &a, cudaStream_t s);
-cudaError_t launch_search_p5_64(int t, const SearchArgs &a, cudaStream_t s);
 int max_blocks_dna32(int t, int wpb);
 size_t fscr_dna32(int lmax);
 size_t fscr_dna64(int lmax);
 size_t fscr_p5_32(int lmax);
-size_t fscr_p5_64(int lmax);
 int max_blocks_dna64(int t, int wpb);
 int max_blocks_p5_32(int t, int wpb);
-int max_blocks_p5_64(int t, int wpb);
 
 cudaError_t launch_search(Layout lay, int t, const SearchArgs &a, cudaStream_t s)
 {
@@ -199,7 +196,7 @@ cudaError_t launch_search(Layout lay, int t, const SearchArgs &a, cudaStream_t s
     case Layout::DNA32: return launch_search_dna32(t, a, s);
     case Layout::DNA64: return launch_search_dna64(t, a, s);
     case Layout::P5_32: return launch_search_p5_32(t, a, s);
-    case Layout::P5_64: return launch_search_p5_64(t, a, s);
+    case Layout::P5_64: break;   // 5-bit letters fit 128-bit keys only up to l = 25
     }
     return cudaErrorInvalidValue;
 }
@@ -210,7 +207,7 @@ size_t search_frontier_bytes(Layout lay, int lmax)
     case Layout::DNA32: return fscr_dna32(lmax);
     case Layout::DNA64: return fscr_dna64(lmax);
     case Layout::P5_32: return fscr_p5_32(lmax);
-    case Layout::P5_64: return fscr_p5_64(lmax);
+    case Layout::P5_64: break;
     }
     return 0;
 }
@@ -221,7 +218,7 @@ int search_max_blocks(Layout lay, int t, int wpb)
     case Layout::DNA32: return max_blocks_dna32(t, wpb);
     case Layout::DNA64: return max_blocks_dna64(t, wpb);
     case Layout::P5_32: return max_blocks_p5_32(t, wpb);
-    case Layout::P5_64: return max_blocks_p5_64(t, wpb);
+    case Layout::P5_64: break;
     }
     return 0;
 }

@@ -31,6 +31,28 @@ namespace search {
 
 using namespace dev;
 
+// With PMS_BOUNDS_CHECK defined (always for the 64-bit-plane layouts, see their
+// translation units) list, l-mer, item and buffer indices are checked before use: a
+// failing check records its line and index, raises kErrBounds and skips the access.
+#ifdef PMS_BOUNDS_CHECK
+#define PMS_OK_IDX(C, idx, lim)                                                         \
+    (((unsigned long long)(idx) < (unsigned long long)(lim))                            \
+         ? true                                                                         \
+         : (pms::search::bad_index((C).stats_dbg, (C).status, __LINE__,                 \
+                                   (unsigned long long)(idx)),                          \
+            false))
+#else
+#define PMS_OK_IDX(C, idx, lim) true
+#endif
+// Debug builds with PMS_DEBUG_DEADLINE stop every warp ~40 s (SM cycles at 2 GHz) into
+// a launch, so that a checked run of a long case ends by itself.
+#ifdef PMS_DEBUG_DEADLINE
+#define PMS_DEADLINE_CYCLES 80000000000ll
+#define PMS_PAST_DEADLINE(C) (clock64() - (C).launch_t0 > PMS_DEADLINE_CYCLES)
+#else
+#define PMS_PAST_DEADLINE(C) false
+#endif
+
 #ifndef PMS_SEARCH_MIN_BLOCKS
 #define PMS_SEARCH_MIN_BLOCKS 5
 #endif
@@ -47,6 +69,7 @@ struct WarpSm {
     int bpos[T + 1];
     int start[T + 1][kRMax];
     int cnt[T + 1][kRMax];
+    int stop;                 // autotuning: the item ran past its cap
 };
 
 struct WarpCounters {
@@ -56,6 +79,14 @@ struct WarpCounters {
 
 template <typename W>
 __device__ __forceinline__ unsigned long long wscale() { return sizeof(W) / 4; }
+
+static __device__ __noinline__ void bad_index(DevStats *st, int *status, int line,
+                                       unsigned long long idx)
+{
+    if (atomicCAS(&st->bad_site, 0ull, (unsigned long long)line) == 0ull)
+        st->bad_value = idx;
+    atomicOr(status, kErrBounds);
+}
 
 template <int NB, typename W>
 struct SearchCtx {
@@ -81,7 +112,28 @@ struct SearchCtx {
     long long budget;
     const unsigned long long *item_next;   // the pass's item counter
     unsigned long long nitems;             // items of this pass
+    int tune_cap;                          // autotuning: items stop at the budget
+    DevStats *stats_dbg;                   // where index checks record a failure
+    long long launch_t0;                   // launch start (checked builds' deadline)
+    uint64_t levels;                       // lists per warp
+    uint64_t nlm;                          // l-mers of this instance (n * L)
 };
+
+// Autotuning only: true (for the whole warp) once the item has run past its budget; the
+// item then stops, and the pass is reported as capped.
+template <int NB, typename W, int T>
+__device__ __forceinline__ bool tune_capped(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &C,
+                                            int lane)
+{
+    if (!C.tune_cap)
+        return false;
+    if (lane == 0 && !S.stop && clock64() - C.t0 > C.budget) {
+        S.stop = 1;
+        atomicOr(C.status, kErrTuneCapped);
+    }
+    __syncwarp();
+    return S.stop != 0;
+}
 
 // Work splitting: an item that has run longer than the budget hands the positions
 // [pos, end) of its range to other warps as up to 64 items with narrower ranges (the
@@ -109,12 +161,22 @@ __device__ bool maybe_donate(const SearchCtx<NB, W> &C, int pos, int end, int la
     const int R = end - pos;
     const int chunk = (R + 63) / 64;
     const int nsub = (R + chunk - 1) / chunk;
-    unsigned long long base = 0;
-    if (lane == 0)
-        base = atomicAdd(C.donate_count, (unsigned long long)nsub);
+    // reserve nsub slots only if they all fit, so the list never holds unwritten slots
+    unsigned long long base = ~0ull;
+    if (lane == 0) {
+        unsigned long long cur = *(volatile unsigned long long *)C.donate_count;
+        while (cur + nsub <= C.donate_cap) {
+            const unsigned long long seen = atomicCAS(C.donate_count, cur, cur + nsub);
+            if (seen == cur) {
+                base = cur;
+                break;
+            }
+            cur = seen;
+        }
+    }
     base = __shfl_sync(kFull, base, 0);
-    if (base + nsub > C.donate_cap)
-        return false;   // no room: keep searching here (the count only sizes the next pass)
+    if (base == ~0ull)
+        return false;   // no room: keep searching here
     for (int i = lane; i < nsub; i += 32) {
         Item sub = C.item;
         const uint16_t a = (uint16_t)(pos + i * chunk);
@@ -204,8 +266,10 @@ __device__ bool build_level2(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &C, int
             const unsigned bal = __ballot_sync(kFull, ok);
             if (ok) {
                 const int at = len + __popc(bal & lanemask_lt());
-                out[at] = ((uint32_t)r << 16) | (uint32_t)j;
-                out_lm[at] = v;
+                if (PMS_OK_IDX(C, at, C.list_cap)) {
+                    out[at] = ((uint32_t)r << 16) | (uint32_t)j;
+                    out_lm[at] = v;
+                }
             }
             len += __popc(bal);
         }
@@ -273,10 +337,12 @@ __device__ bool filter_level(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &C, int
         int row = -1;
         uint32_t e = 0;
         Lm<NB, W> v;
-        if (valid) {
+        if (valid && PMS_OK_IDX(C, idx, C.list_cap)) {
             e = in[idx];
             v = in_lm[idx];
             row = (int)(e >> 16);
+            if (!PMS_OK_IDX(C, row, kRMax))
+                row = 0;
             const W dtv = diff(top, v);
             ok = popc(dtv) <= two_d;
             W div[T];
@@ -300,12 +366,15 @@ __device__ bool filter_level(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &C, int
         const unsigned bal = __ballot_sync(kFull, ok);
         if (ok) {
             const int at = len + __popc(bal & lanemask_lt());
-            out[at] = e;
-            out_lm[at] = v;
+            if (PMS_OK_IDX(C, at, C.list_cap)) {
+                out[at] = e;
+                out_lm[at] = v;
+            }
         }
         len += __popc(bal);
         const unsigned grp = __match_any_sync(kFull, row);
-        if (valid && lane == __ffs(grp) - 1)
+        if (valid && lane == __ffs(grp) - 1 && PMS_OK_IDX(C, k + 1, T + 1) &&
+            PMS_OK_IDX(C, row, kRMax))
             S.cnt[k + 1][row] += __popc(grp & bal);
         __syncwarp();
         const bool last = valid && idx == S.start[k][row] + S.cnt[k][row] - 1;
@@ -416,7 +485,8 @@ __device__ void verify_and_emit(const WarpSm<NB, W, T> &S, const SearchCtx<NB, W
         bool hit = false;
         const int nalive = __popc(__ballot_sync(kFull, alive));
         for (int j0 = 0; j0 < c; j0 += 32) {
-            const Lm<NB, W> vj = list_lm[s0 + (j0 + lane < c ? j0 + lane : 0)];
+            const int vi = s0 + (j0 + lane < c ? j0 + lane : 0);
+            const Lm<NB, W> vj = PMS_OK_IDX(C, vi, C.list_cap) ? list_lm[vi] : list_lm[0];
             const int jn = c - j0 < 32 ? c - j0 : 32;
             for (int jj = 0; jj < jn; jj++) {
                 const Lm<NB, W> v = shfl_lm(vj, jj);
@@ -500,7 +570,11 @@ __device__ void enumerate(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &C, int k,
     for (int b = 0; b < NB; b++)
         M.p[b] = 0;
     unsigned long long nodes = 0;
+    unsigned walk_steps = 0;
     for (;;) {
+        if ((++walk_steps & 63) == 0 && (tune_capped(S, C, lane) ||
+                                          __any_sync(kFull, PMS_PAST_DEADLINE(C))))
+            break;
         // Pick this lane's next node: the next sibling, after backtracking as far as
         // needed, or the root of the next unit.  Every lane then tests one node.
         if (have) {
@@ -520,7 +594,8 @@ __device__ void enumerate(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &C, int k,
                 const int tb = unit / U;
                 int code = unit - tb * U;
                 if (branch) {
-                    st[T - 1] = blist_lm[tb];
+                    st[T - 1] = PMS_OK_IDX(C, S.start[k][br] + tb, C.list_cap) ? blist_lm[tb]
+                                                                               : blist_lm[0];
 #pragma unroll
                     for (int i = 0; i < T - 1; i++)
                         dp[i][T - 1] = diff(st[i], st[T - 1]);
@@ -551,7 +626,7 @@ __device__ void enumerate(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &C, int k,
             }
         }
         const unsigned lb = __ballot_sync(kFull, leaf);
-        if (leaf)
+        if (leaf && PMS_OK_IDX(C, ncand + __popc(lb & lanemask_lt()), kCandBuf))
             S.cand[ncand + __popc(lb & lanemask_lt())] = M;
         ncand += __popc(lb);
         wc.leaves += __popc(lb);
@@ -754,8 +829,11 @@ __device__ void enumerate_frontier(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &
     int ncand = 0;
 
     const int t_end = t_hi < B ? t_hi : B;
+    unsigned steps = 0;
     for (int base = t_lo; base < t_end; base += kTupleRound) {
         if (may_split && base > t_lo && maybe_donate(C, base, t_end, lane, p2))
+            break;
+        if (tune_capped(S, C, lane))
             break;
         const int nb = t_end - base < kTupleRound ? t_end - base : kTupleRound;
         // per-tuple tables, one tuple per lane
@@ -767,7 +845,9 @@ __device__ void enumerate_frontier(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &
                 if (i < k)
                     st[i] = S.stk[i];
             if (branch)
-                st[T - 1] = blist_lm[base + lane];
+                st[T - 1] = PMS_OK_IDX(C, S.start[k][br] + base + lane, C.list_cap)
+                                 ? blist_lm[base + lane]
+                                 : blist_lm[0];
             root_ok = tuple_table<NB, W, T>(st, tk, l, d, tbl_all + (size_t)lane * (l + 1));
         }
         __syncwarp();
@@ -787,6 +867,9 @@ __device__ void enumerate_frontier(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &
         int deepest = __popc(bal) ? 0 : -1;
         __syncwarp();
         while (deepest >= 0) {
+            if ((++steps & 63) == 0 && (tune_capped(S, C, lane) ||
+                                        __any_sync(kFull, PMS_PAST_DEADLINE(C))))
+                break;
             {
                 // deepest non-empty level: the highest lane whose count is non-zero
                 const unsigned hi = __ballot_sync(kFull, cnt_hi > 0);
@@ -829,7 +912,7 @@ __device__ void enumerate_frontier(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &
             }
             const unsigned okb = __ballot_sync(kFull, ok);
             if (p + 1 == l) {
-                if (ok)
+                if (ok && PMS_OK_IDX(C, ncand + __popc(okb & lanemask_lt()), kCandBuf))
                     S.cand[ncand + __popc(okb & lanemask_lt())] = child.M;
                 ncand += __popc(okb);
                 wc.leaves += __popc(okb);
@@ -887,8 +970,10 @@ __device__ void run_item(WarpSm<NB, W, T> &S, SearchCtx<NB, W> &C, const Item &i
                          WarpCounters &wc)
 {
     const InstDesc &I = *C.I;
-    if (lane == 0)
-        S.stk[0] = C.lm[it.x];
+    if (lane == 0) {
+        S.stk[0] = PMS_OK_IDX(C, it.x, C.nlm) ? C.lm[it.x] : C.lm[0];
+        S.stop = 0;
+    }
     if (it.b == 0xFFFF) {  // one string: the d-neighbourhood of x is the answer
         if (lane == 0)
             S.live[1] = 0;
@@ -897,7 +982,9 @@ __device__ void run_item(WarpSm<NB, W, T> &S, SearchCtx<NB, W> &C, const Item &i
         return;
     }
     if (lane == 0)
-        S.stk[1] = C.lm[(size_t)it.b * I.L + it.u];
+        S.stk[1] = PMS_OK_IDX(C, (uint64_t)it.b * I.L + it.u, C.nlm)
+                       ? C.lm[(size_t)it.b * I.L + it.u]
+                       : C.lm[0];
     __syncwarp();
     long long c0 = clock64();
     const bool alive = build_level2(S, C, it.b, lane, wc);
@@ -952,7 +1039,11 @@ __device__ void run_item(WarpSm<NB, W, T> &S, SearchCtx<NB, W> &C, const Item &i
         }
         if (k == 2 && pos > it.lo && maybe_donate(C, pos, end2, lane))
             return;
-        const Lm<NB, W> e = C.planes[(size_t)(k - 2) * C.list_cap + S.start[k][br] + pos];
+        if (tune_capped(S, C, lane))
+            return;
+        const uint64_t pidx = (uint64_t)(k - 2) * C.list_cap + S.start[k][br] + pos;
+        const Lm<NB, W> e = PMS_OK_IDX(C, pidx, C.levels * C.list_cap) ? C.planes[pidx]
+                                                                          : C.planes[0];
         __syncwarp();
         if (lane == 0) {
             S.bpos[k] = pos + 1;
@@ -993,7 +1084,7 @@ __global__ void __launch_bounds__(128, kSearchMinBlocks) search_kernel(
     unsigned long long *key_count, uint64_t key_cap, int *status, DevStats *stats,
     int key_shift, int multi, unsigned char *fscr, uint64_t fscr_stride, int lmax,
     int item_stride, Item *donate, unsigned long long *donate_count, uint64_t donate_cap,
-    long long budget, ItemTrace *trace, void *planes)
+    long long budget, ItemTrace *trace, void *planes, int tune_cap)
 {
     extern __shared__ unsigned char smem_raw[];
     WarpSm<NB, W, T> &S = reinterpret_cast<WarpSm<NB, W, T> *>(smem_raw)[threadIdx.x >> 5];
@@ -1023,6 +1114,10 @@ __global__ void __launch_bounds__(128, kSearchMinBlocks) search_kernel(
     const unsigned long long nitems = (nall + item_stride - 1) / item_stride;
     C.item_next = item_next;
     C.nitems = nitems;
+    C.tune_cap = tune_cap;
+    C.stats_dbg = stats;
+    C.levels = levels;
+    C.launch_t0 = clock64();
     for (;;) {
         unsigned long long it = 0;
         if (lane == 0)
@@ -1030,10 +1125,18 @@ __global__ void __launch_bounds__(128, kSearchMinBlocks) search_kernel(
         it = __shfl_sync(kFull, it, 0);
         if (it >= nitems)
             break;
+        if (!PMS_OK_IDX(C, it * item_stride, item_cap))
+            break;
+        if (PMS_PAST_DEADLINE(C)) {
+            if (lane == 0)
+                bad_index(stats, status, 1000000 + __LINE__, it);
+            break;
+        }
         const Item item = items[it * item_stride];
         C.I = inst + item.inst;
         C.inst = (int)item.inst;
         C.lm = lmers + C.I->lmer_off;
+        C.nlm = (uint64_t)C.I->n * C.I->L;
         const long long it0 = __shfl_sync(kFull, clock64(), 0);
         C.item = item;
         C.t0 = it0;
@@ -1083,7 +1186,7 @@ cudaError_t launch(const SearchArgs &a, cudaStream_t s)
         a.inst, static_cast<const Lm<NB, W> *>(a.lmers), a.items, a.item_count, a.item_cap,
         a.item_next, a.lists, a.list_cap, a.keys, a.key_count, a.key_cap, a.status, a.stats,
         a.key_shift, a.multi, a.fscr, a.fscr_stride, a.lmax, a.item_stride > 0 ? a.item_stride : 1,
-        a.donate, a.donate_count, a.donate_cap, a.budget, a.trace, a.planes);
+        a.donate, a.donate_count, a.donate_cap, a.budget, a.trace, a.planes, a.tune_cap);
     return cudaGetLastError();
 }
 

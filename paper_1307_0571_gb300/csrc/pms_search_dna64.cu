@@ -1,4 +1,9 @@
 // Search kernels for one plane layout (2 bit planes of uint64_t words), thresholds 2..8.
+// Index checks stay on for the 64-bit-plane layouts: a (50,21) run of this layout returned
+// a CUDA error that a checked build of the same run did not reproduce.
+#ifndef PMS_BOUNDS_CHECK
+#define PMS_BOUNDS_CHECK 1
+#endif
 #include "pms_search.cuh"
 
 namespace pms {

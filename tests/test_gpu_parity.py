@@ -85,6 +85,29 @@ def test_long_l_two_words(ctx):
     assert got == want
 
 
+_LONG_L = {}
+
+
+def _long_l_case(l, d, n, m):
+    """DNA l-mers longer than 32 letters (two-word planes) with a many-motif answer."""
+    key = (l, d, n, m)
+    if key not in _LONG_L:
+        inst = synth.planted_instance(78, n, m, l, d)
+        _LONG_L[key] = (inst, oracle.motifs_pms8(inst.seqs, n, m, "ACGT", l, d, t=4))
+    return _LONG_L[key]
+
+
+@pytest.mark.parametrize("l,d,n,m", [(34, 12, 6, 50), (36, 13, 6, 60)])
+@pytest.mark.parametrize("t", [4, 5, 6])
+def test_long_l_thresholds(l, d, n, m, t):
+    # (threshold 3 is left out: common d-neighbourhoods of three such l-mers hold ~1e10
+    # l-mers, out of reach for any implementation of Algorithm 1)
+    inst, want = _long_l_case(l, d, n, m)
+    assert inst.motif in want and len(want) > 10
+    with _ctx(threshold=t) as c:
+        assert c.solve(inst.seqs, n, m, "ACGT", l, d) == want
+
+
 def test_batch_equals_single(ctx):
     from paper_1307_0571_gb300 import pms
     insts = [synth.planted_instance(40 + i, 5 + i, 60 + 13 * i, 8 + (i % 3), 2)
