@@ -23,6 +23,14 @@ region) and `gpu_launches` (kernels of libpms launched in the timed region).
 
 --impl reference times the CPU oracle (the reference arm of this repository) on bounded
 samples of the same workload and prints the same line with "impl": "reference".
+
+--mode batched solves the 64-instance mixed batch ((l,d) in {(13,4),(15,5),(17,6)}, n in
+{10,20,30}, m in {300,600,1000}) as one pms_solve_batch call and as 64 pms_solve calls, and
+reports both throughputs and the per-instance p50/p99 of the single solves.  --mode
+serving replays a Poisson stream of planted requests ((l,d) in {(13,4),...,(19,7)}, n in
+[10,30], m in [300,1200]) through pms_submit/pms_poll at 0.8x the one-at-a-time rate and
+reports p50/p99 latency (arrival to result) and throughput against solving the same
+requests one at a time.  Both check that every result equals the one-at-a-time solve.
 """
 
 from __future__ import annotations
@@ -330,6 +338,99 @@ def run_ours(args) -> None:
         dist.destroy_process_group()
 
 
+def _pct(xs, q):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, int(round(q * (len(xs) - 1))))]
+
+
+def run_batched(args) -> None:
+    from paper_1307_0571_gb300 import pms, synth
+    insts = synth.batched_mix(synth.workload_seed(3, 0), 64)
+    P = [pms.Instance(i.seqs, i.n, i.m, "ACGT", i.l, i.d) for i in insts]
+    ctx = pms.Context(0)
+    singles = [ctx.solve(p.seqs, p.n, p.m, "ACGT", p.l, p.d) for p in P]   # warm-up, tuning
+    seq_s, lat = [], []
+    batch_s = []
+    for _ in range(max(1, args.steps)):
+        t0 = time.perf_counter()
+        for p in P:
+            t1 = time.perf_counter()
+            ctx.solve(p.seqs, p.n, p.m, "ACGT", p.l, p.d)
+            lat.append(time.perf_counter() - t1)
+        seq_s.append(time.perf_counter() - t0)
+        t0 = time.perf_counter()
+        got = ctx.solve_batch(P)
+        batch_s.append(time.perf_counter() - t0)
+        if got != singles:
+            raise SystemExit("batched result differs from single solves")
+    seq, bat = statistics.median(seq_s), statistics.median(batch_s)
+    print(json.dumps({
+        "mode": "batched", "metric": METRIC, "value": len(P) / bat, "unit": UNIT,
+        "n_gpus": 1, "steps": len(batch_s), "higher_is_better": True, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": "64 planted DNA instances, (l,d) in {(13,4),(15,5),(17,6)}, "
+                               "n in {10,20,30}, m in {300,600,1000}",
+                   "motifs": sum(len(x) for x in singles)},
+        "batched_s": bat, "sequential_s": seq,
+        "sequential_instances_per_s": len(P) / seq, "speedup": seq / bat,
+        "single_solve_ms": {"p50": 1000 * _pct(lat, 0.5), "p99": 1000 * _pct(lat, 0.99)},
+        "identical_output": True}), flush=True)
+
+
+def run_serving(args) -> None:
+    from paper_1307_0571_gb300 import pms, synth
+    nreq = args.requests
+    proto = synth.serving_stream(synth.workload_seed(5, 0), nreq, rate_per_s=1.0)
+    insts = [inst for _, inst in proto]
+    ctx = pms.Context(0)
+    # one at a time (also warms up and tunes every class)
+    alone, t_alone = [], []
+    for inst in insts:
+        t0 = time.perf_counter()
+        alone.append(ctx.solve(inst.seqs, inst.n, inst.m, "ACGT", inst.l, inst.d))
+        t_alone.append(time.perf_counter() - t0)
+    seq_rate = len(insts) / sum(t_alone)
+    rate = 0.8 * seq_rate if args.rate < 0 else args.rate
+    if rate > 0:
+        stream = synth.serving_stream(synth.workload_seed(5, 0), nreq, rate_per_s=rate)
+    else:   # saturation: every request arrives at time 0
+        stream = [(0.0, inst) for inst in insts]
+    t0 = time.perf_counter()
+    tickets, arrivals = [], []
+    pending = {}
+    done = {}
+    i = 0
+    while len(done) < len(stream):
+        now = time.perf_counter() - t0
+        while i < len(stream) and stream[i][0] <= now:
+            a, inst = stream[i]
+            tk = ctx.submit(pms.Instance(inst.seqs, inst.n, inst.m, "ACGT", inst.l, inst.d))
+            pending[tk] = (i, a)
+            i += 1
+        for tk in list(pending):
+            r = ctx.poll(tk)
+            if r is not None:
+                j, a = pending.pop(tk)
+                done[j] = (r, time.perf_counter() - t0 - a)
+        time.sleep(0.0005)
+    total = time.perf_counter() - t0
+    if any(done[j][0] != alone[j] for j in range(len(stream))):
+        raise SystemExit("served result differs from the solve alone")
+    lat = [done[j][1] for j in range(len(stream))]
+    print(json.dumps({
+        "mode": "serving", "metric": METRIC, "value": len(stream) / total, "unit": UNIT,
+        "n_gpus": 1, "higher_is_better": True, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": f"{nreq} planted DNA requests, (l,d) in {{(13,4),(15,5),"
+                               "(17,6),(19,7)}, n in [10,30], m in [300,1200], Poisson",
+                   "arrival_rate_per_s": rate if rate > 0 else "all at t=0", "slots": 2},
+        "latency_ms": {"p50": 1000 * _pct(lat, 0.5), "p99": 1000 * _pct(lat, 0.99),
+                       "max": 1000 * max(lat)},
+        "one_at_a_time_instances_per_s": seq_rate,
+        "one_at_a_time_latency_ms": {"p50": 1000 * _pct(t_alone, 0.5),
+                                     "p99": 1000 * _pct(t_alone, 0.99)},
+        "identical_output": True}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -339,6 +440,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="dna_17_6")
     ap.add_argument("--threshold", type=int, default=0, help="0 = autotuned")
+    ap.add_argument("--mode", choices=["single", "batched", "serving"], default="single")
+    ap.add_argument("--requests", type=int, default=120, help="serving mode: requests")
+    ap.add_argument("--rate", type=float, default=-1.0,
+                    help="serving mode: arrivals/s (-1: 0.8x one-at-a-time, 0: all at once)")
     args = ap.parse_args()
     global WORKLOAD, SEED_CONFIG
     WORKLOAD, SEED_CONFIG = WORKLOADS[args.workload]
@@ -346,6 +451,10 @@ def main():
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.mode == "batched":
+        run_batched(args)
+    elif args.mode == "serving":
+        run_serving(args)
     else:
         run_ours(args)
 

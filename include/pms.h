@@ -69,7 +69,7 @@ typedef struct pms_opts {
     int x_begin, x_end;       /* restrict the subproblems to the l-mers x_begin..x_end-1 of
                                  S_1 (Section 2.3); both 0 = all.  Disjoint ranges merged
                                  give the whole set (multi-device sharding by replicas). */
-    int serve_slots;          /* concurrent batches in the serving loop (default 4) */
+    int serve_slots;          /* concurrent batches in the serving loop (default 2) */
     int serve_max_batch;      /* instances per serving batch (default 16) */
 } pms_opts;
 

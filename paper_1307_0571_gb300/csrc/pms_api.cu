@@ -28,9 +28,12 @@ namespace {
 
 // ------------------------------------------------------------------ device buffers
 
+// A device buffer that grows in stream order from the context's memory pool, so growing
+// one serving slot's buffers never synchronises the device under the other slots.
 struct DBuf {
     void *p = nullptr;
     size_t cap = 0;
+    cudaMemPool_t pool = nullptr;
     ~DBuf() { release(); }
     void release()
     {
@@ -39,18 +42,18 @@ struct DBuf {
         p = nullptr;
         cap = 0;
     }
-    // Grow to at least `bytes` (contents are not kept).
-    int ensure(size_t bytes, std::atomic<size_t> &held)
+    // Grow to at least `bytes` on stream s (contents are not kept).
+    int ensure(size_t bytes, std::atomic<size_t> &held, cudaStream_t s)
     {
         if (bytes <= cap)
             return PMS_OK;
         size_t want = std::max(bytes, cap + cap / 2);
         want = (want + 255) & ~size_t(255);
-        release_counted(held);
-        if (cudaMalloc(&p, want) != cudaSuccess) {
+        release_counted(held, s);
+        if (cudaMallocFromPoolAsync(&p, want, pool, s) != cudaSuccess) {
             cudaGetLastError();
             p = nullptr;
-            if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            if (cudaMallocFromPoolAsync(&p, bytes, pool, s) != cudaSuccess) {
                 cudaGetLastError();
                 p = nullptr;
                 return PMS_E_NOMEM;
@@ -61,11 +64,13 @@ struct DBuf {
         held += cap;
         return PMS_OK;
     }
-    void release_counted(std::atomic<size_t> &held)
+    void release_counted(std::atomic<size_t> &held, cudaStream_t s)
     {
         if (p) {
             held -= cap;
-            release();
+            cudaFreeAsync(p, s);
+            p = nullptr;
+            cap = 0;
         }
     }
     template <typename T>
@@ -97,6 +102,7 @@ constexpr long long kTuneItemCap = 20000000;
 // and one per serving slot, so slots run concurrently on their own streams.
 struct Workspace {
     cudaStream_t stream = nullptr;
+    int share = 1;   // the search grid takes 1/share of the GPU's resident blocks
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     DBuf seqs, maps, inst, alpha, lmers, items, lists, fscr, keys, keys_alt, hist, flags,
         out_chars, byte_off, first, last, counters, don0, don1, trace, planes;
@@ -264,6 +270,7 @@ struct pms_ctx {
     pms_opts opts{};
     std::atomic<size_t> held{0};
     size_t budget = 0;
+    cudaMemPool_t pool = nullptr;   // device memory of all workspaces (kept, not returned)
     Workspace main;
     std::mutex solve_mu;
     // threshold autotuner cache: tune_key -> t
@@ -288,6 +295,8 @@ int ws_init(pms_ctx *c, Workspace &w)
 {
     PMS_CU(cudaSetDevice(c->device));
     PMS_CU(cudaStreamCreateWithFlags(&w.stream, cudaStreamNonBlocking));
+    for (DBuf *b : w.all())
+        b->pool = c->pool;
     for (auto &e : w.ev)
         PMS_CU(cudaEventCreate(&e));
     return PMS_OK;
@@ -297,7 +306,9 @@ void ws_free(pms_ctx *c, Workspace &w)
 {
     cudaSetDevice(c->device);
     for (DBuf *b : w.all())
-        b->release_counted(c->held);
+        b->release_counted(c->held, w.stream);
+    if (w.stream)
+        cudaStreamSynchronize(w.stream);
     for (auto &e : w.ev)
         if (e)
             cudaEventDestroy(e);
@@ -409,7 +420,7 @@ int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
             return PMS_E_CUDA;
         if (c->opts.blocks_per_sm)
             per_sm = std::min(per_sm, c->opts.blocks_per_sm);
-        cfg = LaunchCfg{wpb, per_sm * c->sm_count};
+        cfg = LaunchCfg{wpb, std::max(c->sm_count, per_sm * c->sm_count / std::max(1, w.share))};
         return PMS_OK;
     };
     LaunchCfg cfg{};
@@ -428,31 +439,32 @@ int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
     const double want_keys = std::min(6.0 * expect + 65536.0,
                                       (double)std::max<uint64_t>(c->opts.max_motifs, 1) * 8.0);
     uint64_t key_cap = std::max<uint64_t>((uint64_t)want_keys, w.keys.cap / 16);
-    PMS_TRY(w.seqs.ensure(seq_total, c->held));
-    PMS_TRY(w.maps.ensure(256 * (size_t)ninst, c->held));
-    PMS_TRY(w.alpha.ensure(32 * (size_t)ninst, c->held));
-    PMS_TRY(w.inst.ensure(sizeof(InstDesc) * ninst, c->held));
-    PMS_TRY(w.lmers.ensure(lmer_bytes(lay) * lmer_total, c->held));
-    PMS_TRY(w.items.ensure(sizeof(Item) * std::max<uint64_t>(item_cap, 1), c->held));
+    PMS_TRY(w.seqs.ensure(seq_total, c->held, s));
+    PMS_TRY(w.maps.ensure(256 * (size_t)ninst, c->held, s));
+    PMS_TRY(w.alpha.ensure(32 * (size_t)ninst, c->held, s));
+    PMS_TRY(w.inst.ensure(sizeof(InstDesc) * ninst, c->held, s));
+    PMS_TRY(w.lmers.ensure(lmer_bytes(lay) * lmer_total, c->held, s));
+    PMS_TRY(w.items.ensure(sizeof(Item) * std::max<uint64_t>(item_cap, 1), c->held, s));
     const uint64_t fstride = (search_frontier_bytes(lay, lmax) + 255) & ~uint64_t(255);
     // per-warp scratch of a search launch with threshold tt
     auto scratch = [&](int tt, const LaunchCfg &cf) {
         const uint64_t nw = (uint64_t)cf.blocks * cf.warps_per_block;
-        int rc = w.lists.ensure(4ull * nw * search_levels(tt) * list_cap, c->held);
+        int rc = w.lists.ensure(4ull * nw * search_levels(tt) * list_cap, c->held, s);
         if (rc == PMS_OK)
-            rc = w.planes.ensure(lmer_bytes(lay) * nw * search_levels(tt) * list_cap, c->held);
+            rc = w.planes.ensure(lmer_bytes(lay) * nw * search_levels(tt) * list_cap, c->held,
+                                 s);
         if (rc == PMS_OK)
-            rc = w.fscr.ensure(fstride * nw, c->held);
+            rc = w.fscr.ensure(fstride * nw, c->held, s);
         return rc;
     };
     PMS_TRY(scratch(t, cfg));
-    PMS_TRY(w.keys.ensure(16 * key_cap, c->held));
-    PMS_TRY(w.counters.ensure(sizeof(Counters), c->held));
-    PMS_TRY(w.don0.ensure(sizeof(Item) * kDonateCap, c->held));
-    PMS_TRY(w.don1.ensure(sizeof(Item) * kDonateCap, c->held));
-    PMS_TRY(w.first.ensure(8 * (size_t)ninst, c->held));
-    PMS_TRY(w.last.ensure(8 * (size_t)ninst, c->held));
-    PMS_TRY(w.byte_off.ensure(8 * (size_t)ninst, c->held));
+    PMS_TRY(w.keys.ensure(16 * key_cap, c->held, s));
+    PMS_TRY(w.counters.ensure(sizeof(Counters), c->held, s));
+    PMS_TRY(w.don0.ensure(sizeof(Item) * kDonateCap, c->held, s));
+    PMS_TRY(w.don1.ensure(sizeof(Item) * kDonateCap, c->held, s));
+    PMS_TRY(w.first.ensure(8 * (size_t)ninst, c->held, s));
+    PMS_TRY(w.last.ensure(8 * (size_t)ninst, c->held, s));
+    PMS_TRY(w.byte_off.ensure(8 * (size_t)ninst, c->held, s));
     if (c->budget && c->held > c->budget)
         return PMS_E_NOMEM;
 
@@ -489,7 +501,7 @@ int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
     const char *trace_path = std::getenv("PMS_ITEM_TRACE");
     ItemTrace *trace = nullptr;
     if (trace_path && *trace_path && !tune) {
-        PMS_TRY(w.trace.ensure(sizeof(ItemTrace) * std::max<uint64_t>(item_cap, 1), c->held));
+        PMS_TRY(w.trace.ensure(sizeof(ItemTrace) * std::max<uint64_t>(item_cap, 1), c->held, s));
         trace = w.trace.as<ItemTrace>();
     }
     // The search: pass 0 over the items, then passes over the items handed on by
@@ -587,7 +599,7 @@ int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
         uint64_t limit = std::max<uint64_t>(c->opts.max_motifs, 1) * 64;
         if (want > limit || attempt > 4)
             return PMS_E_OVERFLOW;
-        PMS_TRY(w.keys.ensure(16 * want, c->held));
+        PMS_TRY(w.keys.ensure(16 * want, c->held, s));
         key_cap = w.keys.cap / 16;
         if (c->budget && c->held > c->budget)
             return PMS_E_NOMEM;
@@ -610,9 +622,9 @@ int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
     // collect: sort, unique, per-instance ranges
     const size_t nkeys = hc.key_count;
     const size_t ntiles = (nkeys + kSortTile - 1) / kSortTile;
-    PMS_TRY(w.keys_alt.ensure(16 * std::max<size_t>(nkeys, 1), c->held));
-    PMS_TRY(w.hist.ensure(4 * 256 * std::max<size_t>(ntiles, 1), c->held));
-    PMS_TRY(w.flags.ensure(4 * std::max<size_t>(ntiles, 1), c->held));
+    PMS_TRY(w.keys_alt.ensure(16 * std::max<size_t>(nkeys, 1), c->held, s));
+    PMS_TRY(w.hist.ensure(4 * 256 * std::max<size_t>(ntiles, 1), c->held, s));
+    PMS_TRY(w.flags.ensure(4 * std::max<size_t>(ntiles, 1), c->held, s));
     SortScratch scr{w.keys_alt.as<uint64_t>(), w.hist.as<unsigned>(), w.flags.as<unsigned>(),
                     w.keys_alt.cap / 16, w.flags.cap / 4};
     size_t nuniq = 0;
@@ -639,7 +651,7 @@ int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
     }
     char *out_dev = nullptr;
     if (bo.host) {
-        PMS_TRY(w.out_chars.ensure(std::max<uint64_t>(bytes, 1), c->held));
+        PMS_TRY(w.out_chars.ensure(std::max<uint64_t>(bytes, 1), c->held, s));
         out_dev = w.out_chars.as<char>();
     } else {
         out_dev = bo.dev_motifs;
@@ -835,18 +847,41 @@ void serve_worker(pms_ctx *c, Workspace *w)
             c->q_cv.wait(lk, [&] { return c->stop || !c->pending.empty(); });
             if (c->stop && c->pending.empty())
                 return;
-            // estimated device bytes of a request: strings, l-mers, items, raw motifs
-            size_t room = c->budget > c->held ? c->budget - c->held : 0;
+            // Admission: the cheapest pending request first (Appendix D cost estimate), then
+            // others no more than 8x costlier, within the batch size and the memory still
+            // free under the budget (strings, l-mers, items, raw motifs), so light requests
+            // are not held behind heavy ones.
+            const size_t room = c->budget > c->held ? c->budget - c->held : 0;
+            auto cost = [](const Request &r) {
+                const int k = (int)r.alphabet.size();
+                return model_cost(r.n, r.m, r.l, r.d, k,
+                                  model_threshold(r.n, r.m, r.l, r.d, k));
+            };
+            auto bytes = [](const Request &r) {
+                const size_t L = (size_t)(r.m - r.l + 1);
+                return (size_t)r.n * r.m * 2 + (size_t)r.n * L * 40 + L * L * 8;
+            };
+            std::vector<std::pair<double, size_t>> order;
+            for (size_t i = 0; i < c->pending.size(); i++)
+                order.emplace_back(cost(c->pending[i]), i);
+            std::sort(order.begin(), order.end());
+            std::vector<size_t> take;
             size_t est_total = 0;
-            while (!c->pending.empty() && (int)batch.size() < max_batch) {
-                const Request &r = c->pending.front();
-                size_t L = (size_t)(r.m - r.l + 1);
-                size_t est = (size_t)r.n * r.m * 2 + (size_t)r.n * L * 40 + L * L * 8;
-                if (!batch.empty() && est_total + est > room)
+            for (auto &oc : order) {
+                if ((int)take.size() >= max_batch)
+                    break;
+                if (!take.empty() && oc.first > 8.0 * order[0].first)
+                    break;
+                const size_t est = bytes(c->pending[oc.second]);
+                if (!take.empty() && est_total + est > room)
                     break;
                 est_total += est;
-                batch.push_back(std::move(c->pending.front()));
-                c->pending.pop_front();
+                take.push_back(oc.second);
+            }
+            std::sort(take.begin(), take.end());
+            for (size_t j = take.size(); j-- > 0;) {
+                batch.push_back(std::move(c->pending[take[j]]));
+                c->pending.erase(c->pending.begin() + (long)take[j]);
             }
             for (auto &r : batch)
                 c->in_flight[r.ticket] = 1;
@@ -958,7 +993,7 @@ int pms_create(pms_ctx **out, int device, const pms_opts *opts)
     if (!c->opts.max_motifs)
         c->opts.max_motifs = 1ull << 26;
     if (!c->opts.serve_slots)
-        c->opts.serve_slots = 4;
+        c->opts.serve_slots = 2;
     if (!c->opts.serve_max_batch)
         c->opts.serve_max_batch = 16;
     if (c->opts.threshold && (c->opts.threshold < 2 || c->opts.threshold > kTMax)) {
@@ -972,8 +1007,20 @@ int pms_create(pms_ctx **out, int device, const pms_opts *opts)
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
     c->budget = c->opts.mem_budget ? c->opts.mem_budget : free_b / 4 * 3;
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    if (cudaMemPoolCreate(&c->pool, &props) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return PMS_E_CUDA;
+    }
+    uint64_t keep = UINT64_MAX;   // freed blocks stay in the pool for the next solve
+    cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
     if (ws_init(c, c->main) != PMS_OK) {
         ws_free(c, c->main);
+        cudaMemPoolDestroy(c->pool);
         delete c;
         return PMS_E_CUDA;
     }
@@ -997,6 +1044,8 @@ void pms_destroy(pms_ctx *c)
     for (auto &f : c->finished)
         std::free(f.second.res.motifs);
     ws_free(c, c->main);
+    if (c->pool)
+        cudaMemPoolDestroy(c->pool);
     delete c;
 }
 
