@@ -704,77 +704,67 @@ __device__ __forceinline__ void rot_selectors(int tk, uint32_t &r1, uint32_t &r2
     r2 = tk == 4 ? 0x1032u : tk == 3 ? 0x4102u : 0x4444u;
 }
 
-// Limits of one tuple for prefix length q = l down to 0, and the letters of its l-mers
-// at each position: tbl[q] = {letters at position q-1, pair limits (i,i+1), pair limits
-// (i,i+2), triple limits (i,i+1,i+2)} for prefix length q, so testing a child at position
-// p reads the single entry tbl[p+1].  Returns false when the tuple itself fails the pair
-// or triple condition (no common neighbour, Theorem 1).
+// Limit tables of one round of tuples, built by all lanes at once.  Entry b * (l + 1) + q,
+// for tuple b and prefix length q, is {letters of the tuple's l-mers at position q-1,
+// pair limits (i,i+1), pair limits (i,i+2), triple limits (i,i+1,i+2)}, so testing a
+// child at position p reads the single entry for q = p+1.  Every limit needs only a
+// count over the suffix from position q: one popcount of a difference mask restricted to
+// positions q.., so the entries are independent.  Returns the mask of tuples whose root
+// already fails the pair or triple condition (no common d-neighbour, Theorem 1).
 template <int NB, typename W, int T>
-__device__ bool tuple_table(const Lm<NB, W> (&st)[T], int tk, int l, int d, uint4 *tbl)
+__device__ uint32_t build_tables(const SearchCtx<NB, W> &C, const Lm<NB, W> (&stack)[T],
+                                 const W (&dps)[T][T], int k, const Lm<NB, W> *blist,
+                                 uint64_t bpos, int nb, int tk, int l, int d, W lmask,
+                                 uint4 *tbl, int lane)
 {
-    W dp[T][T];
+    uint32_t bad = 0;
+    const int E = nb * (l + 1);
+    for (int idx = lane; idx < E; idx += 32) {
+        const int b = idx / (l + 1);
+        const int q = idx - b * (l + 1);
+        Lm<NB, W> st[T];
+        W dp[T][T];
 #pragma unroll
-    for (int i = 0; i < T; i++)
+        for (int i = 0; i < T; i++) {
+            st[i] = stack[i];
 #pragma unroll
-        for (int j = i + 1; j < T; j++)
-            if (j < tk)
-                dp[i][j] = diff(st[i], st[j]);
-    int hs1[T], hs2[T], cs[T];
-#pragma unroll
-    for (int i = 0; i < T; i++)
-        hs1[i] = hs2[i] = cs[i] = 0;
-    int cs4 = 0;   // Cd of the four l-mers over positions q.. (Lemma 1), when tk == 4
-    bool ok = true;
-    for (int q = l; q >= 0; q--) {
-        if (q < l && T >= 4 && tk == 4) {
-            const W d01 = dp[0][1], d02 = dp[0][2], d03 = dp[0][3];
-            const W d12 = dp[1][2], d13 = dp[1][3], d23 = dp[2][3];
-            const int has2 = (int)((~(d01 & d02 & d03 & d12 & d13 & d23) >> q) & 1);
-            const int has3 = (int)((~((d01 | d02) & (d01 | d03) & (d02 | d03) & (d12 | d13)) >> q) & 1);
-            const int all4 = (int)((~(d01 | d02 | d03) >> q) & 1);
-            cs4 += 3 - has2 - has3 - all4;
+            for (int j = 0; j < T; j++)
+                dp[i][j] = dps[i][j];
         }
-        if (q < l) {
+        if (tk > k) {   // the tuple's last l-mer comes from the branch row
+            st[T - 1] = PMS_OK_IDX(C, bpos + b, C.list_cap) ? blist[b] : blist[0];
 #pragma unroll
-            for (int i = 0; i < T; i++) {
-                if (i < tk && tk >= 2) {
-                    const int j = (i + 1) % tk;
-                    const W dij = i < j ? dp[i][j] : dp[j][i];
-                    hs1[i] += (int)((dij >> q) & 1);
-                }
-                if (i < tk && tk == 4) {
-                    const int j = (i + 2) % 4;
-                    const W dij = i < j ? dp[i][j] : dp[j][i];
-                    hs2[i] += (int)((dij >> q) & 1);
-                }
-                if (i < tk && tk >= 3) {
-                    int a = i, b = (i + 1) % tk, c = (i + 2) % tk;
-                    // sort (a, b, c) so the pair masks come from the upper triangle
-                    if (a > b) { int t0 = a; a = b; b = t0; }
-                    if (b > c) { int t0 = b; b = c; c = t0; }
-                    if (a > b) { int t0 = a; a = b; b = t0; }
-                    const W x = dp[a][b], y = dp[a][c], z = dp[b][c];
-                    cs[i] += (int)(((x | y) >> q) & 1) + (int)(((x & y & z) >> q) & 1);
-                }
-            }
+            for (int i = 0; i < T - 1; i++)
+                dp[i][T - 1] = diff(st[i], st[T - 1]);
         }
+        const W sfx = lmask & ~low_mask<W>(q);
+        bool ok = true;
         uint32_t lim1 = 0x7F7F7F7Fu, lim2 = 0xFF7F7F7Fu, lim3 = 0x7F7F7F7Fu, codes = 0;
 #pragma unroll
         for (int i = 0; i < T; i++) {
             if (i < tk) {
                 const int sh = 8 * i;
                 if (tk >= 2) {
-                    const int v = 2 * d - hs1[i];
+                    const int j = (i + 1) % tk;
+                    const W dij = i < j ? dp[i][j] : dp[j][i];
+                    const int v = 2 * d - popc(dij & sfx);
                     ok = ok && v >= 0;
                     lim1 = (lim1 & ~(0xFFu << sh)) | ((uint32_t)(v < 0 ? 0 : v) << sh);
                 }
                 if (tk == 4) {
-                    const int v = 2 * d - hs2[i];
+                    const int j = (i + 2) % 4;
+                    const W dij = i < j ? dp[i][j] : dp[j][i];
+                    const int v = 2 * d - popc(dij & sfx);
                     ok = ok && v >= 0;
                     lim2 = (lim2 & ~(0xFFu << sh)) | ((uint32_t)(v < 0 ? 0 : v) << sh);
                 }
                 if (tk >= 3) {
-                    const int v = 3 * d - cs[i];
+                    int a = i, b2 = (i + 1) % tk, c = (i + 2) % tk;
+                    if (a > b2) { int t0 = a; a = b2; b2 = t0; }
+                    if (b2 > c) { int t0 = b2; b2 = c; c = t0; }
+                    if (a > b2) { int t0 = a; a = b2; b2 = t0; }
+                    const W x = dp[a][b2], y = dp[a][c], z = dp[b2][c];
+                    const int v = 3 * d - popc((x | y) & sfx) - popc(x & y & z & sfx);
                     ok = ok && v >= 0;
                     lim3 = (lim3 & ~(0xFFu << sh)) | ((uint32_t)(v < 0 ? 0 : v) << sh);
                 }
@@ -783,14 +773,23 @@ __device__ bool tuple_table(const Lm<NB, W> (&st)[T], int tk, int l, int d, uint
             }
         }
         if (T >= 4 && tk == 4) {
-            // pairs (i, i+2) repeat in bytes 2 and 3; byte 3 carries 4d - Cd(suffix)
+            // Cd of four l-mers over positions q.. (Lemma 1): per column 4 minus the
+            // largest number of equal letters
+            const W d01 = dp[0][1], d02 = dp[0][2], d03 = dp[0][3];
+            const W d12 = dp[1][2], d13 = dp[1][3], d23 = dp[2][3];
+            const W has2 = ~(d01 & d02 & d03 & d12 & d13 & d23);
+            const W has3 = ~((d01 | d02) & (d01 | d03) & (d02 | d03) & (d12 | d13));
+            const W all4 = ~(d01 | d02 | d03);
+            const int cs4 = 3 * (l - q) - popc(has2 & sfx) - popc(has3 & sfx) - popc(all4 & sfx);
             const int v = 4 * d - cs4;
             ok = ok && v >= 0;
             lim2 = (lim2 & 0x00FFFFFFu) | ((uint32_t)(v < 0 ? 0 : v) << 24);
         }
-        tbl[q] = make_uint4(codes, lim1, lim2, lim3);
+        tbl[idx] = make_uint4(codes, lim1, lim2, lim3);
+        if (q == 0 && !ok)
+            bad |= 1u << b;
     }
-    return ok;
+    return __reduce_or_sync(kFull, bad);
 }
 
 // Algorithm 1 + isMotif for up to four l-mers per tuple; arguments as in enumerate().
@@ -814,6 +813,24 @@ __device__ void enumerate_frontier(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &
     const Lm<NB, W> *blist_lm =
         branch ? C.planes + (size_t)(k - 2) * C.list_cap + S.start[k][br] : C.planes;
 
+    const W lmask = low_mask<W>(l);
+    Lm<NB, W> stack[T];
+    W dps[T][T];
+#pragma unroll
+    for (int i = 0; i < T; i++) {
+        if (i < k)
+            stack[i] = S.stk[i];
+        else
+#pragma unroll
+            for (int b2 = 0; b2 < NB; b2++)
+                stack[i].p[b2] = 0;
+    }
+#pragma unroll
+    for (int i = 0; i < T; i++)
+#pragma unroll
+        for (int j = 0; j < T; j++)
+            dps[i][j] = (i < j && j < k) ? diff(stack[i], stack[j]) : W(0);
+
     uint32_t r1, r2;
     rot_selectors(tk, r1, r2);
     uint32_t lim0 = 0x7F7F7F7Fu, used = 0;
@@ -836,20 +853,11 @@ __device__ void enumerate_frontier(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &
         if (tune_capped(S, C, lane))
             break;
         const int nb = t_end - base < kTupleRound ? t_end - base : kTupleRound;
-        // per-tuple tables, one tuple per lane
-        bool root_ok = false;
-        if (lane < nb) {
-            Lm<NB, W> st[T];
-#pragma unroll
-            for (int i = 0; i < T; i++)
-                if (i < k)
-                    st[i] = S.stk[i];
-            if (branch)
-                st[T - 1] = PMS_OK_IDX(C, S.start[k][br] + base + lane, C.list_cap)
-                                 ? blist_lm[base + lane]
-                                 : blist_lm[0];
-            root_ok = tuple_table<NB, W, T>(st, tk, l, d, tbl_all + (size_t)lane * (l + 1));
-        }
+        __syncwarp();   // the previous round's nodes are all read
+        const uint32_t bad = build_tables<NB, W, T>(
+            C, stack, dps, k, blist_lm + base, branch ? (uint64_t)S.start[k][br] + base : 0, nb,
+            tk, l, d, lmask, tbl_all, lane);
+        const bool root_ok = lane < nb && !((bad >> lane) & 1);
         __syncwarp();
         // roots: empty prefix, no mismatches
         unsigned bal = __ballot_sync(kFull, root_ok);
@@ -864,22 +872,14 @@ __device__ void enumerate_frontier(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &
         }
         // lane i keeps the node counts of levels i and i + 32
         int cnt_lo = lane == 0 ? __popc(bal) : 0, cnt_hi = 0;
-        int deepest = __popc(bal) ? 0 : -1;
+        // the deepest non-empty level and its node count (warp-uniform)
+        int deepest = __popc(bal) ? 0 : -1, have = __popc(bal);
         __syncwarp();
         while (deepest >= 0) {
             if ((++steps & 63) == 0 && (tune_capped(S, C, lane) ||
                                         __any_sync(kFull, PMS_PAST_DEADLINE(C))))
                 break;
-            {
-                // deepest non-empty level: the highest lane whose count is non-zero
-                const unsigned hi = __ballot_sync(kFull, cnt_hi > 0);
-                const unsigned lo = __ballot_sync(kFull, cnt_lo > 0);
-                deepest = hi ? 63 - __clz(hi) : lo ? 31 - __clz(lo) : -1;
-                if (deepest < 0)
-                    break;
-            }
             const int p = deepest;
-            const int have = __shfl_sync(kFull, p < 32 ? cnt_lo : cnt_hi, p & 31);
             const int c = have < chunk ? have : chunk;
             const int first = have - c;
             if (lane == (p & 31)) {
@@ -938,6 +938,20 @@ __device__ void enumerate_frontier(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &
                         cnt_hi = __popc(okb);
                 }
                 __syncwarp();
+            }
+            if (p + 1 < l && okb) {
+                deepest = p + 1;
+                have = __popc(okb);
+            } else if (first > 0) {
+                have = first;
+            } else {
+                // level p is used up: the next is the highest lane whose count is non-zero
+                const unsigned hi = __ballot_sync(kFull, cnt_hi > 0);
+                const unsigned lo = __ballot_sync(kFull, cnt_lo > 0);
+                deepest = hi ? 63 - __clz(hi) : lo ? 31 - __clz(lo) : -1;
+                have = deepest < 0 ? 0
+                                   : __shfl_sync(kFull, deepest < 32 ? cnt_lo : cnt_hi,
+                                                 deepest & 31);
             }
         }
     }
