@@ -96,7 +96,9 @@ constexpr uint64_t kDonateCap = 1u << 20;
 constexpr long long kItemBudget = 4000000;
 // Autotuning: an item running longer than this (cycles, ~10 ms) stops and marks the
 // candidate threshold as capped.
-constexpr long long kTuneItemCap = 20000000;
+constexpr long long kTuneItemCap = 1500000000;   // cycles, first tuning candidate
+constexpr unsigned long long kTuneItemsPerWarp = 8;   // tuning sample size per search warp
+constexpr double kMaxCyclesPerMs = 2.1e6;             // SM cycles per ms at the highest clock
 
 // Everything one pipeline run needs on the device; a context owns one for blocking calls
 // and one per serving slot, so slots run concurrently on their own streams.
@@ -114,12 +116,18 @@ struct Workspace {
     }
 };
 
-// A failing CUDA call returns PMS_E_CUDA; with PMS_DEBUG set in the environment the
-// call, its place and CUDA's error string also go to stderr.
-void report_cuda(cudaError_t e, const char *what, int line)
+// PMS_DEBUG set in the environment: diagnostics go to stderr.
+bool debug_on()
 {
     static const bool on = std::getenv("PMS_DEBUG") != nullptr;
-    if (on)
+    return on;
+}
+
+// A failing CUDA call returns PMS_E_CUDA; with PMS_DEBUG set the call, its place and
+// CUDA's error string also go to stderr.
+void report_cuda(cudaError_t e, const char *what, int line)
+{
+    if (debug_on())
         std::fprintf(stderr, "libpms: %s failed at pms_api.cu:%d: %s (%d)\n", what, line,
                      cudaGetErrorString(e), (int)e);
 }
@@ -362,7 +370,7 @@ struct BatchOut {
 struct Tune {
     std::vector<int> cand;
     int best = 0;
-    std::vector<float> ms;
+    std::vector<float> ms;   // device time of each candidate's sample (infinite: capped)
 };
 
 int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
@@ -523,10 +531,8 @@ int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
                           &dc->key_count, key_cap, &dc->status, &dc->stats, key_bits, multi,
                           cf, w.fscr.as<unsigned char>(), fstride, lmax,
                           first_pass ? stride : 1, don[out], &dc->donate_count[out],
-                          cap ? 0 : kDonateCap, cap ? cap : kItemBudget,
-                          first_pass ? trace : nullptr, w.planes.p, cap ? 1 : 0};
-            if (cap)
-                sa.donate = nullptr;
+                          kDonateCap, kItemBudget, first_pass ? trace : nullptr, w.planes.p,
+                          cap};
             PMS_CU(launch_search(lay, tt, sa, s));
             launches++;
             unsigned long long handed = 0;
@@ -543,19 +549,25 @@ int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
         unsigned long long nitems = 0;
         PMS_CU(copy(&nitems, &dc->item_count, sizeof nitems, cudaMemcpyDeviceToHost, s));
         PMS_CU(cudaStreamSynchronize(s));
-        const int stride = (int)std::max<unsigned long long>(1, nitems / 1024);
-        // The first candidate runs under a generous safety cap; each later one is capped at
-        // 4x the slowest item of the best uncapped candidate so far, and a capped candidate
-        // is out (some item of it ran far longer than that item).
-        float best_ms = INFINITY;
-        unsigned long long best_item = 0;
+        // A candidate's cost is the device time of the search over every stride-th item,
+        // with work splitting as in a full run.  The sample holds at least kTuneItemsPerWarp
+        // items per search warp, so the passes run at the occupancy of a full run (at low
+        // occupancy, latency that a full run hides would count against the list filter).
+        // The first candidate runs under a generous per-item safety cap; each later one is
+        // capped at the best time so far in cycles at the highest SM clock, so a capped
+        // candidate (out) is one with a single item slower than the best whole pass.
+        double best_ms = INFINITY;
         tune->ms.clear();
         for (int tt : tune->cand) {
             LaunchCfg cf{};
             PMS_TRY(shape(tt, cf));
             PMS_TRY(scratch(tt, cf));
-            const long long cap = tune->best ? std::max<long long>(kTuneItemCap, 4 * (long long)best_item)
-                                             : 8 * kTuneItemCap;
+            const unsigned long long warps = (unsigned long long)cf.blocks * cf.warps_per_block;
+            const int stride = (int)std::max<unsigned long long>(
+                1, nitems / std::max<unsigned long long>(1024, kTuneItemsPerWarp * warps));
+            const long long cap =
+                tune->best ? std::min<long long>(kTuneItemCap, (long long)(best_ms * kMaxCyclesPerMs))
+                           : kTuneItemCap;
             PMS_CU(cudaMemsetAsync(&dc->status, 0, sizeof(int), s));
             PMS_CU(cudaMemsetAsync(&dc->stats, 0, sizeof(DevStats), s));
             PMS_CU(cudaEventRecord(w.ev[1], s));
@@ -568,9 +580,12 @@ int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
             cudaEventElapsedTime(&ms, w.ev[1], w.ev[2]);
             const bool capped = (tc.status & kErrTuneCapped) != 0;
             tune->ms.push_back(capped ? INFINITY : ms);
+            if (debug_on())
+                std::fprintf(stderr, "pms autotune: l=%d d=%d n=%d m=%d t=%d stride=%d ms=%.3f%s\n",
+                             ins[0].l, ins[0].d, ins[0].n, ins[0].m, tt, stride, ms,
+                             capped ? " (capped)" : "");
             if (!capped && ms < best_ms) {
                 best_ms = ms;
-                best_item = tc.stats.item_max;
                 tune->best = tt;
             }
         }
@@ -727,9 +742,9 @@ int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
     return PMS_OK;
 }
 
-// Autotuner: the first time an instance class (tune_key) is seen, time
-// the search on a sample of its items for the thresholds around the Appendix D model
-// and cache the fastest.  The motif set does not depend on the threshold.
+// Autotuner: the first time an instance class (tune_key) is seen, time the search on a
+// sample of its items for the thresholds around the Appendix D model and cache the
+// fastest.  The motif set does not depend on the threshold.
 void autotune(pms_ctx *c, Workspace &w, const Prep &p)
 {
     const auto key = tune_key(p);

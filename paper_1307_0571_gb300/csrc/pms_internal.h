@@ -164,7 +164,8 @@ struct SearchArgs {
     long long budget;         // cycles an item runs before it hands on the rest of its range
     ItemTrace *trace;         // per-item records of the first pass, or null
     void *planes;             // scratch: the l-mers of the list entries (same shape as lists)
-    int tune_cap;             // autotuning: stop any item still running after `budget`
+    long long tune_cap;       // autotuning: stop any item still running after this many
+                              // cycles (0: no cap)
 };
 
 // Lists each search warp keeps for threshold t (levels 2..t-1, at least one).  Every list

@@ -112,24 +112,28 @@ struct SearchCtx {
     long long budget;
     const unsigned long long *item_next;   // the pass's item counter
     unsigned long long nitems;             // items of this pass
-    int tune_cap;                          // autotuning: items stop at the budget
+    long long tune_cap;                    // autotuning: items stop after this many cycles
     DevStats *stats_dbg;                   // where index checks record a failure
     long long launch_t0;                   // launch start (checked builds' deadline)
     uint64_t levels;                       // lists per warp
     uint64_t nlm;                          // l-mers of this instance (n * L)
 };
 
-// Autotuning only: true (for the whole warp) once the item has run past its budget; the
-// item then stops, and the pass is reported as capped.
+// Autotuning only: true (for the whole warp) once the launch has run past the tuning
+// cap, here or in another warp; the item then stops, and the pass is reported as capped.
 template <int NB, typename W, int T>
 __device__ __forceinline__ bool tune_capped(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &C,
                                             int lane)
 {
     if (!C.tune_cap)
         return false;
-    if (lane == 0 && !S.stop && clock64() - C.t0 > C.budget) {
-        S.stop = 1;
-        atomicOr(C.status, kErrTuneCapped);
+    if (lane == 0 && !S.stop) {
+        if (clock64() - C.launch_t0 > C.tune_cap) {
+            S.stop = 1;
+            atomicOr(C.status, kErrTuneCapped);
+        } else if (*(volatile const int *)C.status & kErrTuneCapped) {
+            S.stop = 1;
+        }
     }
     __syncwarp();
     return S.stop != 0;
@@ -479,8 +483,17 @@ __device__ void verify_and_emit(const WarpSm<NB, W, T> &S, const SearchCtx<NB, W
     bool alive = lane < ncand;
     const Lm<NB, W> *list_lm = k >= 2 ? C.planes + (size_t)(k - 2) * C.list_cap : C.planes;
     while (rows && __any_sync(kFull, alive)) {
-        const int r = __ffsll((long long)rows) - 1;
-        rows &= rows - 1;
+        // next, the row with the fewest l-mers left: the cheapest to scan and the one
+        // most likely to have no neighbour of a candidate
+        const unsigned k0 = ((rows >> lane) & 1)
+                                ? ((unsigned)min(S.cnt[k][lane], (1 << 25) - 1) << 6) | lane
+                                : ~0u;
+        const unsigned k1 = ((rows >> (lane + 32)) & 1)
+                                ? ((unsigned)min(S.cnt[k][lane + 32], (1 << 25) - 1) << 6) |
+                                      (lane + 32)
+                                : ~0u;
+        const int r = (int)(__reduce_min_sync(kFull, k0 < k1 ? k0 : k1) & 63u);
+        rows &= ~(1ull << r);
         const int s0 = S.start[k][r], c = S.cnt[k][r];
         bool hit = false;
         const int nalive = __popc(__ballot_sync(kFull, alive));
@@ -1098,7 +1111,7 @@ __global__ void __launch_bounds__(128, kSearchMinBlocks) search_kernel(
     unsigned long long *key_count, uint64_t key_cap, int *status, DevStats *stats,
     int key_shift, int multi, unsigned char *fscr, uint64_t fscr_stride, int lmax,
     int item_stride, Item *donate, unsigned long long *donate_count, uint64_t donate_cap,
-    long long budget, ItemTrace *trace, void *planes, int tune_cap)
+    long long budget, ItemTrace *trace, void *planes, long long tune_cap)
 {
     extern __shared__ unsigned char smem_raw[];
     WarpSm<NB, W, T> &S = reinterpret_cast<WarpSm<NB, W, T> *>(smem_raw)[threadIdx.x >> 5];
@@ -1135,7 +1148,9 @@ __global__ void __launch_bounds__(128, kSearchMinBlocks) search_kernel(
     for (;;) {
         unsigned long long it = 0;
         if (lane == 0)
-            it = atomicAdd(item_next, 1ull);
+            it = (tune_cap && (*(volatile const int *)status & kErrTuneCapped))
+                     ? nitems   // a tuning pass already capped: nothing more to learn
+                     : atomicAdd(item_next, 1ull);
         it = __shfl_sync(kFull, it, 0);
         if (it >= nitems)
             break;
