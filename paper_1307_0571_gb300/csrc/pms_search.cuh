@@ -252,17 +252,32 @@ __device__ bool build_level2(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &C, int
     Lm<NB, W> *out_lm = C.planes;
     int len = 0;
     uint64_t live = 0;
+    // the l-mers of the next chunk are loaded before the current chunk is tested
+    int r_next = b == 1 ? 2 : 1;
+    Lm<NB, W> v_next;
+#pragma unroll
+    for (int b2 = 0; b2 < NB; b2++)
+        v_next.p[b2] = 0;
+    if (r_next < I.n && lane < I.L)
+        v_next = C.lm[(size_t)r_next * I.L + lane];
     for (int r = 1; r < I.n; r++) {
         if (r == b)
             continue;
         const int s0 = len;
-        const Lm<NB, W> *row = C.lm + (size_t)r * I.L;
         for (int j0 = 0; j0 < I.L; j0 += 32) {
             const int j = j0 + lane;
             bool ok = false;
-            Lm<NB, W> v;
+            const Lm<NB, W> v = v_next;
+            {
+                int rn = r, jn = j0 + 32;
+                if (jn >= I.L) {
+                    rn = r + 1 == b ? r + 2 : r + 1;
+                    jn = 0;
+                }
+                if (rn < I.n && jn + lane < I.L)
+                    v_next = C.lm[(size_t)rn * I.L + jn + lane];
+            }
             if (j < I.L) {
-                v = row[j];
                 const W dxv = diff(x, v), duv = diff(u, v);
                 ok = popc(dxv) <= two_d && popc(duv) <= two_d &&
                      popc(dxu | dxv) + popc(dxu & dxv & duv) <= three_d;
@@ -333,20 +348,39 @@ __device__ bool filter_level(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &C, int
     S.cnt[k + 1][lane + 32] = 0;
     __syncwarp();
     int len = 0;
+    // element vi of the input: the level-k list without the branch row; the entries of a
+    // row are contiguous, so a row ends where the next element's row differs
+    uint32_t e_next = 0;
+    Lm<NB, W> v_next;
+#pragma unroll
+    for (int b2 = 0; b2 < NB; b2++)
+        v_next.p[b2] = 0;
+    {
+        const int idx = lane < bs ? lane : lane + bc;
+        if (lane < total && PMS_OK_IDX(C, idx, C.list_cap)) {
+            e_next = in[idx];
+            v_next = in_lm[idx];
+        }
+    }
     for (int c0 = 0; c0 < total; c0 += 32) {
         const int vi = c0 + lane;
         const bool valid = vi < total;
-        const int idx = vi < bs ? vi : vi + bc;
+        const uint32_t e = e_next;
+        const Lm<NB, W> v = v_next;
+        // load the next chunk before working on this one
+        {
+            const int vn = vi + 32;
+            const int idx = vn < bs ? vn : vn + bc;
+            if (vn < total && PMS_OK_IDX(C, idx, C.list_cap)) {
+                e_next = in[idx];
+                v_next = in_lm[idx];
+            }
+        }
+        int row = valid ? (int)(e >> 16) : -1;
+        if (valid && !PMS_OK_IDX(C, row, kRMax))
+            row = 0;
         bool ok = false;
-        int row = -1;
-        uint32_t e = 0;
-        Lm<NB, W> v;
-        if (valid && PMS_OK_IDX(C, idx, C.list_cap)) {
-            e = in[idx];
-            v = in_lm[idx];
-            row = (int)(e >> 16);
-            if (!PMS_OK_IDX(C, row, kRMax))
-                row = 0;
+        if (valid) {
             const W dtv = diff(top, v);
             ok = popc(dtv) <= two_d;
             W div[T];
@@ -376,13 +410,26 @@ __device__ bool filter_level(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &C, int
             }
         }
         len += __popc(bal);
-        const unsigned grp = __match_any_sync(kFull, row);
-        if (valid && lane == __ffs(grp) - 1 && PMS_OK_IDX(C, k + 1, T + 1) &&
-            PMS_OK_IDX(C, row, kRMax))
-            S.cnt[k + 1][row] += __popc(grp & bal);
+        // survivors per row: the lanes of one row form a segment of the chunk; its last
+        // lane adds the segment's count and, when the row ends there, checks it
+        const int first_next = __shfl_sync(kFull, c0 + 32 < total ? (int)(e_next >> 16) : -1, 0);
+        const int prow = __shfl_up_sync(kFull, row, 1);
+        int nrow = __shfl_down_sync(kFull, row, 1);
+        if (lane == 31)
+            nrow = first_next;
+        const unsigned starts = __ballot_sync(kFull, valid && (lane == 0 || prow != row));
+        const bool row_end = valid && (nrow != row || vi + 1 == total);
+        bool empty = false;
+        if (row_end || (valid && lane == 31)) {
+            const unsigned le = (lanemask_lt() << 1) | 1u;
+            const int s0 = 31 - __clz(starts & le);
+            const int add = __popc(bal & le & ~((1u << s0) - 1u));
+            const int tot = S.cnt[k + 1][row] + add;
+            S.cnt[k + 1][row] = tot;
+            empty = row_end && tot == 0;
+        }
         __syncwarp();
-        const bool last = valid && idx == S.start[k][row] + S.cnt[k][row] - 1;
-        if (__any_sync(kFull, last && S.cnt[k + 1][row] == 0)) {
+        if (__any_sync(kFull, empty)) {
             const int done = c0 + 32 < total ? c0 + 32 : total;
             wc.compares += (unsigned long long)done * (k + 1);
             wc.ops += (unsigned long long)done * (op_filter(NB, k) + (T >= 4 && k == 2 ? op_lemma4() : 0)) * wscale<W>();
