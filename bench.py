@@ -65,6 +65,9 @@ WORKLOAD, SEED_CONFIG = WORKLOADS["dna_17_6"]   # seeds synth.workload_seed(conf
 def _workload_name(w):
     return (f"planted DNA (l,d)=({w['l']},{w['d']}), n={w['n']}, m={w['m']} "
             f"(one instance per step)")
+# dram__bytes_read.sum + dram__bytes_write.sum of the first search pass of a (17,6)
+# solve at threshold 4 (one ncu --set full capture of the current kernel)
+SEARCH_TRAFFIC_17_6 = 2.875e9 + 6.028e9
 SM_COUNT = 152
 INT_OPS_PER_CLK_SM = 128         # 4 SMSPs x 32 lanes issue-limited integer ops
 CPU_SAMPLE_X = 24                # l-mers of S_1 in the CPU baseline sample
@@ -319,7 +322,10 @@ def run_ours(args) -> None:
         "roofline": {"kernel": "search_kernel", "bound": "alu",
                      "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12,
                      "unit": "Tintop/s", "frac": achieved_ops / peak_ops,
-                     "traffic": None,
+                     # DRAM bytes of the first search pass of a (17,6) solve (ncu capture
+                     # in profiles/search_kernel_dna_17_6.md); other workloads: not captured
+                     "traffic": (SEARCH_TRAFFIC_17_6 if WORKLOAD is WORKLOADS["dna_17_6"][0]
+                                 and stats[0].threshold == 4 else None),
                      "peak_note": f"{SM_COUNT} SMs x {INT_OPS_PER_CLK_SM} int ops/clk x "
                                   f"{sm_max:.0f} MHz (derived; no measured integer peak)"},
         "e2e": {"value": world * args.steps / e2e_s, "unit": UNIT,
