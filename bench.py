@@ -67,7 +67,7 @@ def _workload_name(w):
             f"(one instance per step)")
 # dram__bytes_read.sum + dram__bytes_write.sum of the first search pass of a (17,6)
 # solve at threshold 4 (one ncu --set full capture of the current kernel)
-SEARCH_TRAFFIC_17_6 = 2.875e9 + 6.028e9
+SEARCH_TRAFFIC_17_6 = 21.204e9 + 16.017e9
 SM_COUNT = 152
 INT_OPS_PER_CLK_SM = 128         # 4 SMSPs x 32 lanes issue-limited integer ops
 CPU_SAMPLE_X = 24                # l-mers of S_1 in the CPU baseline sample

@@ -54,9 +54,12 @@ using namespace dev;
 #endif
 
 #ifndef PMS_SEARCH_MIN_BLOCKS
-#define PMS_SEARCH_MIN_BLOCKS 5
+#define PMS_SEARCH_MIN_BLOCKS 8
 #endif
-// Resident 4-warp blocks per SM the register allocation must allow.
+// Resident 4-warp blocks per SM the register allocation must allow.  The search is bound
+// by dependent integer ops, so more resident warps beat the spills they cost: 8 blocks
+// (64 registers, 32 warps per SM) ran (17,6) 10% faster than 5 (96 registers); 10 and 12
+// spilled too much.
 constexpr int kSearchMinBlocks = PMS_SEARCH_MIN_BLOCKS;
 
 template <int NB, typename W, int T>
