@@ -9,6 +9,7 @@ compiles it with gcc, maps letters to codes and back, and calls it through ctype
     hd(u, v)                         Hamming distance (Section 1)
     cd(tuple)                        consensus total distance (Definition 1, Section 2.4)
     theorem1(a, b, c, da, db, dc)    the three-l-mer condition (Theorem 1)
+    theorem1_witness(a, b, c, ...)   a common neighbour built as in Theorem 1's proof
     neighborhood(tuple, d, alphabet) common d-neighbourhood by Algorithm 1 (Appendix A)
     is_motif(M, seqs, d)             the motif predicate (Section 1)
     motifs_def(...)                  the motif set by definition (Section 1)
@@ -54,6 +55,7 @@ def _load():
             lib.oracle_hd.argtypes = [u8p, u8p, ctypes.c_int]
             lib.oracle_cd.argtypes = [u8p, ctypes.c_int, ctypes.c_int]
             lib.oracle_theorem1.argtypes = [u8p, u8p, u8p] + [ctypes.c_int] * 4
+            lib.oracle_theorem1_witness.argtypes = [u8p, u8p, u8p] + [ctypes.c_int] * 4 + [u8p]
             lib.oracle_neighborhood.argtypes = [u8p] + [ctypes.c_int] * 4 + [
                 ctypes.POINTER(u8p)]
             lib.oracle_neighborhood.restype = ctypes.c_longlong
@@ -106,6 +108,19 @@ def theorem1(a: str, b: str, c: str, da: int, db: int, dc: int,
     lib = _load()
     return bool(lib.oracle_theorem1(_codes(a, alphabet)[1], _codes(b, alphabet)[1],
                                     _codes(c, alphabet)[1], len(a), da, db, dc))
+
+
+def theorem1_witness(a: str, b: str, c: str, da: int, db: int, dc: int,
+                     alphabet: str = "ACGT") -> str | None:
+    """An l-mer M with Hd(M,a) <= da, Hd(M,b) <= db, Hd(M,c) <= dc, built column by
+    column as in the proof of Theorem 1 (Section 2.4); None when the theorem's conditions
+    fail (then no such M exists)."""
+    lib = _load()
+    l = len(a)
+    buf = (ctypes.c_uint8 * max(l, 1))()
+    ok = lib.oracle_theorem1_witness(_codes(a, alphabet)[1], _codes(b, alphabet)[1],
+                                     _codes(c, alphabet)[1], l, da, db, dc, buf)
+    return "".join(alphabet[buf[i]] for i in range(l)) if ok else None
 
 
 def neighborhood(tuple_: list[str], d: int, alphabet: str = "ACGT") -> list[str]:

@@ -11,6 +11,7 @@
  *   oracle_hd            Hamming distance (Section 1).
  *   oracle_cd            Consensus total distance Cd(T) (Definition 1, Section 2.4).
  *   oracle_theorem1      The three-l-mer condition of Theorem 1 (Section 2.4).
+ *   oracle_theorem1_witness  A common neighbour built as in the proof of Theorem 1.
  *   oracle_neighborhood  Algorithm 1 (Appendix A), common d-neighbourhood of a tuple.
  *   oracle_is_motif      The motif predicate of Section 1 for one l-mer.
  *   oracle_motifs_def    The motif set straight from the definition (Section 1): every motif
@@ -110,6 +111,78 @@ int oracle_theorem1(const uint8_t *a, const uint8_t *b, const uint8_t *c, int l,
     if (oracle_hd(b, c, l) > db + dc)
         return 0;
     return cd3(a, b, c, l) <= da + db + dc;
+}
+
+/*
+ * The "if" half of Theorem 1 made constructive, following its proof (Section 2.4).  Columns
+ * are typed by which l-mer is the odd one out: N0 all equal, N_i only T_i differs (the
+ * other two agree), N4 all three distinct; n_i counts them.
+ *   Case 1, some n_i >= d_i: M copies T_i except in d_i columns of type N_i, where it takes
+ *     the letter the other two share.  Then Hd(M,T_i) = d_i and, M lying on a shortest
+ *     path from T_i to T_j, Hd(M,T_j) = Hd(T_i,T_j) - d_i <= d_j.
+ *   Case 2, every n_i < d_i: M takes the majority letter in every column of type N0..N3,
+ *     so Hd(M,T_i) = n_i plus its mismatches in N4 columns; then for each i it copies T_i
+ *     in max(0, n_i + n4 - d_i) of the N4 columns not yet used.  The conditions of the
+ *     theorem are exactly what makes these choices fit in the n4 columns.
+ * Writes M (l codes) and returns 1 when the conditions of Theorem 1 hold; returns 0 and
+ * leaves M untouched otherwise.
+ */
+int oracle_theorem1_witness(const uint8_t *a, const uint8_t *b, const uint8_t *c, int l,
+                            int da, int db, int dc, uint8_t *M)
+{
+    const uint8_t *T[3] = {a, b, c};
+    const int dd[3] = {da, db, dc};
+    int type_n[5] = {0, 0, 0, 0, 0};
+    if (!oracle_theorem1(a, b, c, l, da, db, dc))
+        return 0;
+    for (int k = 0; k < l; k++) {
+        const int e12 = a[k] == b[k], e13 = a[k] == c[k], e23 = b[k] == c[k];
+        type_n[e12 && e13 ? 0 : e23 ? 1 : e13 ? 2 : e12 ? 3 : 4]++;
+    }
+    for (int i = 0; i < 3; i++) {
+        if (type_n[i + 1] >= dd[i]) {   /* case 1 with T_i */
+            const int j = (i + 1) % 3;
+            int left = dd[i];
+            for (int k = 0; k < l; k++) {
+                const int e12 = a[k] == b[k], e13 = a[k] == c[k], e23 = b[k] == c[k];
+                const int ty = e12 && e13 ? 0 : e23 ? 1 : e13 ? 2 : e12 ? 3 : 4;
+                if (ty == i + 1 && left > 0) {
+                    M[k] = T[j][k];
+                    left--;
+                } else {
+                    M[k] = T[i][k];
+                }
+            }
+            return 1;
+        }
+    }
+    /* case 2 */
+    int want[3];
+    for (int i = 0; i < 3; i++) {
+        want[i] = type_n[i + 1] + type_n[4] - dd[i];
+        if (want[i] < 0)
+            want[i] = 0;
+    }
+    for (int k = 0; k < l; k++) {
+        const int e12 = a[k] == b[k], e13 = a[k] == c[k], e23 = b[k] == c[k];
+        const int ty = e12 && e13 ? 0 : e23 ? 1 : e13 ? 2 : e12 ? 3 : 4;
+        if (ty == 1) {
+            M[k] = b[k];
+        } else if (ty != 4) {
+            M[k] = a[k];
+        } else {
+            int pick = 0;
+            while (pick < 3 && want[pick] == 0)
+                pick++;
+            if (pick < 3) {
+                M[k] = T[pick][k];
+                want[pick]--;
+            } else {
+                M[k] = a[k];
+            }
+        }
+    }
+    return 1;
 }
 
 /* ------------------------------------------------------------ growable motif list */

@@ -101,6 +101,59 @@ def test_theorem1_random_triples(oracle_lib, alphabet):
             a, b, c, da, db, dc, alphabet)
 
 
+def _hd(u, v):
+    return sum(x != y for x, y in zip(u, v))
+
+
+@pytest.mark.parametrize("l", [1, 2, 3, 4, 5])
+def test_theorem1_witness_exhaustive_column_types(oracle_lib, l):
+    # The construction in the proof of Theorem 1 yields a common neighbour exactly when
+    # one exists (brute force over all 4^l l-mers), for every column-type multiset.
+    for a, b, c, _ in brute.column_type_triples(l):
+        cand = brute.all_lmers(4, l)
+        dist = [(cand != brute.codes(s, "ACGT")).sum(axis=1) for s in (a, b, c)]
+        for da, db, dc in itertools.product(range(0, l + 1), repeat=3):
+            truth = bool(((dist[0] <= da) & (dist[1] <= db) & (dist[2] <= dc)).any())
+            M = oracle_lib.theorem1_witness(a, b, c, da, db, dc)
+            assert (M is not None) == truth, (a, b, c, da, db, dc)
+            if M is not None:
+                assert _hd(M, a) <= da and _hd(M, b) <= db and _hd(M, c) <= dc
+
+
+@pytest.mark.parametrize("alphabet", ["ACGT", "ACDEFGHIKLMNPQRSTVWY"])
+def test_theorem1_witness_long_lmers(oracle_lib, alphabet):
+    # At lengths brute force cannot reach: triples planted around a random M0 (so a common
+    # neighbour exists and the witness must be one), and random triples with budgets near
+    # the pair limits (the witness exists exactly when the conditions of Theorem 1 hold,
+    # and then it is a common neighbour).  Both cases of the proof occur.
+    rng = random.Random(11)
+    for _ in range(300):
+        l = rng.randint(15, 64)
+        m0 = [rng.choice(alphabet) for _ in range(l)]
+        trip, budgets = [], []
+        for _ in range(3):
+            di = rng.randint(0, l // 2)
+            s = list(m0)
+            for pos in rng.sample(range(l), di):
+                s[pos] = rng.choice([x for x in alphabet if x != m0[pos]])
+            trip.append("".join(s))
+            budgets.append(di)
+        M = oracle_lib.theorem1_witness(*trip, *budgets, alphabet)
+        assert M is not None
+        assert all(_hd(M, t) <= di for t, di in zip(trip, budgets))
+    for _ in range(300):
+        l = rng.randint(15, 64)
+        a, b, c = ("".join(rng.choice(alphabet) for _ in range(l)) for _ in range(3))
+        hab, hac, hbc = _hd(a, b), _hd(a, c), _hd(b, c)
+        da = rng.randint(0, l)
+        db = max(0, hab - da + rng.randint(-2, 2))
+        dc = max(0, max(hac - da, hbc - db) + rng.randint(-2, 2))
+        M = oracle_lib.theorem1_witness(a, b, c, da, db, dc, alphabet)
+        assert (M is not None) == oracle_lib.theorem1(a, b, c, da, db, dc, alphabet)
+        if M is not None:
+            assert _hd(M, a) <= da and _hd(M, b) <= db and _hd(M, c) <= dc
+
+
 # ---------------------------------------------------------------- Algorithm 1
 
 @pytest.mark.parametrize("l,d,alphabet", [(5, 0, "ACGT"), (6, 2, "ACGT"), (8, 3, "ACGT"),
