@@ -38,6 +38,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -71,6 +72,7 @@ SEARCH_TRAFFIC_17_6 = 21.204e9 + 16.017e9
 SM_COUNT = 152
 INT_OPS_PER_CLK_SM = 128         # 4 SMSPs x 32 lanes issue-limited integer ops
 CPU_SAMPLE_X = 24                # l-mers of S_1 in the CPU baseline sample
+CPU_SAMPLE_X1 = 2                # l-mers of S_1 in its one-thread sample
 REF_SAMPLE_X = 0                 # l-mers of S_1 per reference-arm step (0: one per core)
 
 
@@ -164,9 +166,29 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(inst, l, d, n, m, sample_x=CPU_SAMPLE_X) -> dict:
+def _cpu_model() -> str:
+    """The host CPU as /proc/cpuinfo names it ("model name", or the Arm part number)."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            info = f.read().splitlines()
+    except OSError:
+        return platform.machine()
+    fields = {}
+    for ln in info:
+        k, _, v = ln.partition(":")
+        fields.setdefault(k.strip(), v.strip())
+    if fields.get("model name"):
+        return fields["model name"]
+    if fields.get("CPU part"):
+        return (f"{platform.machine()} CPU implementer {fields.get('CPU implementer', '?')} "
+                f"part {fields['CPU part']}")
+    return platform.machine()
+
+
+def cpu_baseline(inst, l, d, n, m, sample_x=CPU_SAMPLE_X, sample_x1=CPU_SAMPLE_X1) -> dict:
     """The PMS8 oracle (plain CPU C, all host cores) on the subproblems of the first
-    `sample_x` l-mers of S_1, scaled to whole instances per second."""
+    `sample_x` l-mers of S_1, scaled to whole instances per second; and the same on one
+    thread for the first `sample_x1` l-mers."""
     import oracle
     oracle.build()
     L = m - l + 1
@@ -175,10 +197,18 @@ def cpu_baseline(inst, l, d, n, m, sample_x=CPU_SAMPLE_X) -> dict:
     oracle.motifs_pms8(inst.seqs, n, m, "ACGT", l, d, t=3, x_begin=0, x_end=sample_x,
                        threads=cores)
     dt = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.motifs_pms8(inst.seqs, n, m, "ACGT", l, d, t=3, x_begin=0, x_end=sample_x1,
+                       threads=1)
+    dt1 = time.perf_counter() - t0
     return {"value": (sample_x / L) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "cpu_model": _cpu_model(),
             "sample": f"PMS8 oracle (oracle/pms_oracle.c, threshold 3) on the subproblems of "
                       f"l-mers 0..{sample_x - 1} of S_1 ({sample_x}/{L} of one instance) "
-                      f"took {dt:.2f} s; value scales that to whole instances"}
+                      f"took {dt:.2f} s; value scales that to whole instances",
+            "one_thread": {"value": (sample_x1 / L) / dt1, "unit": UNIT, "cores": 1,
+                           "sample": f"l-mers 0..{sample_x1 - 1} of S_1 on one thread took "
+                                     f"{dt1:.2f} s"}}
 
 
 def run_reference(args) -> None:
@@ -212,6 +242,7 @@ def run_reference(args) -> None:
         "config": {"workload": _workload_name(WORKLOAD), "sample": f"{per_step} l-mers of S_1 per step",
                    "parallelism": "host threads"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "cpu_model": _cpu_model(),
                          "sample": f"each step: PMS8 oracle on the subproblems of l-mers "
                                    f"0..{per_step - 1} of S_1 of a fresh instance"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
