@@ -96,7 +96,10 @@ constexpr uint64_t kDonateCap = 1u << 20;
 constexpr long long kItemBudget = 4000000;
 // Autotuning: an item running longer than this (cycles, ~10 ms) stops and marks the
 // candidate threshold as capped.
-constexpr long long kTuneItemCap = 1500000000;   // cycles, first tuning candidate
+// Cycles a tuning launch may run for the first candidate (~10 s).  Later candidates are
+// capped at the best time so far; a cap below a legitimate pass (large instances such as
+// (21,8), whose sample passes take seconds) would reject every candidate.
+constexpr long long kTuneItemCap = 20000000000LL;
 constexpr unsigned long long kTuneItemsPerWarp = 8;   // tuning sample size per search warp
 constexpr double kMaxCyclesPerMs = 2.1e6;             // SM cycles per ms at the highest clock
 
@@ -553,9 +556,9 @@ int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
         // with work splitting as in a full run.  The sample holds at least kTuneItemsPerWarp
         // items per search warp, so the passes run at the occupancy of a full run (at low
         // occupancy, latency that a full run hides would count against the list filter).
-        // The first candidate runs under a generous per-item safety cap; each later one is
-        // capped at the best time so far in cycles at the highest SM clock, so a capped
-        // candidate (out) is one with a single item slower than the best whole pass.
+        // The first candidate's launches run under a generous safety cap; each later one's
+        // are capped at the best time so far in cycles at the highest SM clock, so a
+        // capped candidate (out) has a single launch slower than the best whole sample.
         double best_ms = INFINITY;
         tune->ms.clear();
         for (int tt : tune->cand) {
