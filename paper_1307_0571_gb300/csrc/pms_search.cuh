@@ -11,17 +11,20 @@
 //    balance across the GPU.
 //  * Level k (stack size k) keeps, for each string not on the stack, the list of its
 //    surviving l-mers: one flat list per level in the warp's scratch, rows in string
-//    order, entries (string << 16 | position).  Filtering is lane-parallel over that
-//    flat list with warp-ballot compaction; per-row counts come from __match_any_sync.
+//    order, entries (string << 16 | position) with the l-mer's planes inline.  Filtering
+//    is lane-parallel over that flat list with warp-ballot compaction; a row's lanes form
+//    a segment of each 32-element chunk, whose last lane adds the row's survivors.
 //  * The threshold T is the stack size of the pattern-driven part.  The stack is filtered
 //    up to size T-1; then every l-mer u' of the smallest remaining row closes one tuple
 //    (stack, u') whose common neighbourhood is enumerated directly, and its leaves are
 //    verified against the level-(T-1) lists.  The last filter level is skipped because it
 //    rarely empties a row and would cost more than the enumeration it saves; the result
 //    is the same, since a neighbour's witness in every row survives all necessary filters.
-//  * Enumeration: the tuples of one level node, times the subtrees below a P-letter
-//    prefix, form units that lanes take round-robin; each lane walks its unit depth first
-//    (one child test per step) and leaves go to a shared buffer verified 32 at a time.
+//  * Enumeration, up to four l-mers per tuple (T <= 4): a frontier of nodes with packed
+//    byte budgets, expanded a chunk at a time from the deepest level, one child per lane,
+//    against per-tuple limit tables.  Larger tuples: the tuples times the subtrees below
+//    a P-letter prefix form units that lanes take round-robin and walk depth first.  In
+//    both, leaves go to a shared buffer verified 32 at a time.
 #pragma once
 
 #include "pms_device.cuh"
