@@ -108,6 +108,36 @@ def test_long_l_thresholds(l, d, n, m, t):
         assert c.solve(inst.seqs, n, m, "ACGT", l, d) == want
 
 
+_A32 = "ABCDEFGHIJKLMNOPQRSTUVWXYZ012345"
+
+
+@pytest.mark.parametrize("n,m,l,d,alphabet,seed", [
+    (5, 70, 64, 3, "ACGT", 11),              # longest DNA l-mers (two 32-bit words a plane)
+    (4, 40, 25, 2, synth.PROTEIN, 12),       # longest l for 20 letters (5 bits a letter)
+    (4, 40, 5, 2, _A32, 13),                 # the largest alphabet
+    (4, 40, 25, 1, _A32, 14),                # largest alphabet at its longest l
+])
+def test_size_limits_vs_definition(ctx, n, m, l, d, alphabet, seed):
+    inst = synth.planted_instance(seed, n, m, l, d, alphabet)
+    want = oracle.motifs_def(inst.seqs, n, m, alphabet, l, d)
+    assert inst.motif in want
+    assert ctx.solve(inst.seqs, n, m, alphabet, l, d) == want
+
+
+def test_beyond_size_limits(ctx):
+    from paper_1307_0571_gb300 import pms
+    dna = synth.random_instance(3, 2, 80, 65, 3)
+    prot = synth.random_instance(3, 2, 40, 26, 3, synth.PROTEIN)
+    for args in [(dna.seqs, 2, 80, "ACGT", 65, 3),                      # l > 64
+                 (prot.seqs, 2, 40, synth.PROTEIN, 26, 3),              # 5 * 26 bits > 128
+                 (b"AC" * 65, 65, 2, "ACGT", 2, 0),                     # n > 64
+                 (b"ACGT", 1, 4, "A", 2, 0),                            # one-letter alphabet
+                 (b"A" * 8, 1, 8, "".join(chr(48 + i) for i in range(33)), 2, 0)]:
+        with pytest.raises(pms.PMSError) as e:
+            ctx.solve(*args)
+        assert e.value.code == pms.PMS_E_INVAL, args[3:]
+
+
 def test_batch_equals_single(ctx):
     from paper_1307_0571_gb300 import pms
     insts = [synth.planted_instance(40 + i, 5 + i, 60 + 13 * i, 8 + (i % 3), 2)
