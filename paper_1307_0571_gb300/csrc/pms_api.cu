@@ -548,7 +548,7 @@ int run_group(pms_ctx *c, Workspace &w, std::vector<Prep> &ins, BatchOut &bo,
     };
     Counters hc{};
     if (tune) {
-        // Section 2.2: the threshold is found empirically on a small subset of the tuples.
+        // Section 2.2 picks the threshold by trying the search on a sample of the work.
         unsigned long long nitems = 0;
         PMS_CU(copy(&nitems, &dc->item_count, sizeof nitems, cudaMemcpyDeviceToHost, s));
         PMS_CU(cudaStreamSynchronize(s));

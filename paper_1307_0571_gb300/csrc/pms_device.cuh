@@ -1,7 +1,7 @@
 // Device helpers shared by the CUDA translation units of libpms: packed l-mers as bit
 // planes and their distance primitives, warp utilities.
 //
-// Packing (Section 2.1, "Compress l-mers"): plane b of an l-mer holds bit b of every
+// Packing (Section 2.1, compressed l-mers): plane b of an l-mer holds bit b of every
 // letter's code, bit p for position p.  The positions where two l-mers differ are
 // OR_b(a_b XOR b_b), so Hd is one popcount per word; this replaces the paper's table of
 // 2^16 precomputed group counts.

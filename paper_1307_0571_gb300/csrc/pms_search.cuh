@@ -320,7 +320,7 @@ __device__ bool build_level2(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &C, int
 // l-mer s, Cd(s, top, v) <= 3d (Theorem 1 with budgets d,d,d; the pair conditions with
 // earlier l-mers hold from earlier levels).  With two l-mers below the top, v must also
 // meet Lemma 1 for all four: Cd(x, u, top, v) <= 4d.  Returns false as soon as a row
-// empties (Section 2: "If any row becomes empty ... try a different l-mer").
+// empties (Section 2: an empty row ends this stack and the search moves on).
 template <int NB, typename W, int T>
 __device__ bool filter_level(WarpSm<NB, W, T> &S, const SearchCtx<NB, W> &C, int k, int lane,
                              WarpCounters &wc)
