@@ -47,7 +47,7 @@ enum {
     PMS_E_ALPHABET = -2,  /* a sequence byte is not in the alphabet */
     PMS_E_NOMEM = -3,     /* device or host allocation failed, or memory budget exceeded */
     PMS_E_OVERFLOW = -4,  /* the motif set is larger than opts.max_motifs */
-    PMS_E_TIMEOUT = -5,   /* a bounded wait expired (pms_poll with a timeout) */
+    PMS_E_TIMEOUT = -5,   /* a bounded wait expired (pms_wait) */
     PMS_E_CUDA = -6,      /* CUDA error, or no usable sm_103a device */
     PMS_E_BUSY = -7,      /* serving queue full */
     PMS_E_NOTFOUND = -8   /* unknown ticket */
@@ -182,6 +182,14 @@ int pms_submit(pms_ctx *ctx, const pms_instance *inst, uint64_t *ticket);
  * to the caller; the ticket is retired) when finished; *done = 0 otherwise.  The return
  * value is the solve's own status once done. */
 int pms_poll(pms_ctx *ctx, uint64_t ticket, pms_result *out, int *done);
+
+/* Serving: block until a ticket finishes, for at most timeout_ms milliseconds (negative:
+ * no limit).  When it finishes, *out is filled (ownership passes to the caller; the
+ * ticket is retired) and the return value is the solve's own status.  PMS_E_TIMEOUT: the
+ * wait expired, nothing changed and the ticket stays valid.  PMS_E_NOTFOUND: unknown or
+ * retired ticket, or the context is being destroyed.  Any thread may wait; each ticket's
+ * result goes to one caller.  (A serving convenience; the paper has no counterpart.) */
+int pms_wait(pms_ctx *ctx, uint64_t ticket, pms_result *out, int timeout_ms);
 
 /* Release the motif buffer of a result (safe on zeroed results). */
 void pms_result_free(pms_result *res);

@@ -289,7 +289,8 @@ struct pms_ctx {
     std::map<std::tuple<int, int, int, int, int>, int> tune;
     // serving
     std::mutex q_mu;
-    std::condition_variable q_cv;
+    std::condition_variable q_cv;      // workers: requests pending or stop
+    std::condition_variable done_cv;   // pms_wait: a batch finished or stop
     std::deque<Request> pending;
     std::unordered_map<uint64_t, Finished> finished;
     std::unordered_map<uint64_t, int> in_flight;
@@ -943,6 +944,7 @@ void serve_worker(pms_ctx *c, Workspace *w)
                 c->finished[batch[i].ticket] = Finished{pre_rc[i], res[i]};
             }
         }
+        c->done_cv.notify_all();
     }
 }
 
@@ -1055,6 +1057,7 @@ void pms_destroy(pms_ctx *c)
         c->stop = true;
     }
     c->q_cv.notify_all();
+    c->done_cv.notify_all();
     for (auto &t : c->workers)
         t.join();
     for (auto &w : c->slots)
@@ -1197,6 +1200,35 @@ int pms_poll(pms_ctx *c, uint64_t ticket, pms_result *out, int *done)
     int rc = it->second.rc;
     c->finished.erase(it);
     *done = 1;
+    return rc;
+}
+
+int pms_wait(pms_ctx *c, uint64_t ticket, pms_result *out, int timeout_ms)
+{
+    if (!c || !out)
+        return PMS_E_INVAL;
+    std::unique_lock<std::mutex> lk(c->q_mu);
+    auto known = [&] {
+        if (c->finished.count(ticket) || c->in_flight.count(ticket))
+            return true;
+        for (auto &r : c->pending)
+            if (r.ticket == ticket)
+                return true;
+        return false;
+    };
+    if (!known())
+        return PMS_E_NOTFOUND;
+    auto ready = [&] { return c->stop || c->finished.count(ticket) > 0; };
+    if (timeout_ms < 0)
+        c->done_cv.wait(lk, ready);
+    else if (!c->done_cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready))
+        return PMS_E_TIMEOUT;
+    auto it = c->finished.find(ticket);
+    if (it == c->finished.end())
+        return PMS_E_NOTFOUND;   // the context is being destroyed
+    *out = it->second.res;
+    const int rc = it->second.rc;
+    c->finished.erase(it);
     return rc;
 }
 

@@ -31,7 +31,7 @@ PMS_E_BUSY = -7
 PMS_E_NOTFOUND = -8
 
 EXPORTS = ["pms_create", "pms_destroy", "pms_solve", "pms_solve_batch", "pms_solve_device",
-           "pms_submit", "pms_poll", "pms_result_free", "pms_strerror",
+           "pms_submit", "pms_poll", "pms_wait", "pms_result_free", "pms_strerror",
            "pms_autotune_entries", "pms_autotune_reset", "pms_solve_device_noalloc"]
 
 
@@ -103,6 +103,7 @@ def load() -> ctypes.CDLL:
         lib.pms_submit.argtypes = [ctypes.c_void_p, P(pms_instance), P(ctypes.c_uint64)]
         lib.pms_poll.argtypes = [ctypes.c_void_p, ctypes.c_uint64, P(pms_result),
                                  P(ctypes.c_int)]
+        lib.pms_wait.argtypes = [ctypes.c_void_p, ctypes.c_uint64, P(pms_result), ctypes.c_int]
         lib.pms_result_free.argtypes = [P(pms_result)]
         lib.pms_result_free.restype = None
         lib.pms_strerror.argtypes = [ctypes.c_int]
@@ -270,6 +271,18 @@ class Context:
         if rc != PMS_OK:
             self.lib.pms_result_free(ctypes.byref(res))
             raise PMSError(rc, "pms_poll")
+        return _take(self.lib, res)
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        """The sorted motif list once the ticket finishes; None if timeout_ms passes first
+        (negative: wait without limit)."""
+        res = pms_result()
+        rc = self.lib.pms_wait(self.h, ticket, ctypes.byref(res), int(timeout_ms))
+        if rc == PMS_E_TIMEOUT:
+            return None
+        if rc != PMS_OK:
+            self.lib.pms_result_free(ctypes.byref(res))
+            raise PMSError(rc, "pms_wait")
         return _take(self.lib, res)
 
     def autotune_entries(self) -> int:

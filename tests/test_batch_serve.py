@@ -5,8 +5,8 @@ The mixed batch is 64 planted DNA instances with (l,d) in {(13,4),(15,5),(17,6)}
 ways: the batched solve equals the single solve; on the subproblems of the two l-mers of
 S_1 at the planted copy (Section 2.3) it equals the stored oracle set; and a sample of its
 motifs satisfies the Section 1 predicate directly.  The serving loop (pms_submit /
-pms_poll) runs requests that arrive while others are on the GPU, and every result must
-equal the same instance solved alone.
+pms_poll, pms_wait) runs requests that arrive while others are on the GPU, and every
+result must equal the same instance solved alone.
 """
 
 from __future__ import annotations
@@ -92,4 +92,19 @@ def test_poll_unknown_ticket(ctx):
     from paper_1307_0571_gb300 import pms
     with pytest.raises(pms.PMSError) as e:
         ctx.poll(10 ** 12)
+    assert e.value.code == pms.PMS_E_NOTFOUND
+
+
+def test_wait_times_out_then_returns_the_result(ctx):
+    from paper_1307_0571_gb300 import pms
+    inst = synth.planted_instance(synth.workload_seed(2, 1), 20, 600, 17, 6)
+    alone = ctx.solve(inst.seqs, 20, 600, "ACGT", 17, 6)   # also tunes the class
+    t = ctx.submit(pms.Instance(inst.seqs, 20, 600, "ACGT", 17, 6))
+    assert ctx.wait(t, timeout_ms=0) is None     # a (17,6) solve takes ~150 ms
+    assert ctx.wait(t) == alone
+    with pytest.raises(pms.PMSError) as e:       # the ticket is retired
+        ctx.wait(t, timeout_ms=0)
+    assert e.value.code == pms.PMS_E_NOTFOUND
+    with pytest.raises(pms.PMSError) as e:
+        ctx.wait(10 ** 12, timeout_ms=10)
     assert e.value.code == pms.PMS_E_NOTFOUND
