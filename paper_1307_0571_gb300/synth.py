@@ -2,8 +2,8 @@
 
 The paper evaluates only on synthetic inputs: n i.i.d. uniform strings of length m over
 an alphabet, with one random l-mer planted at a random position of every string and each
-planted copy changed in d positions (Section 1, "PMS algorithms are typically tested on
-instances generated as follows"; Section 3 uses the same recipe).  This module is the one
+planted copy changed in d positions (the recipe of Section 1, which Section 3 uses for
+every measurement).  This module is the one
 place that draws those inputs; it holds none of the motif-search arithmetic, so both the
 CUDA path and the CPU oracle can be fed from it.
 
